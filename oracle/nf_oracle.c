@@ -1,0 +1,214 @@
+/*
+ * nf_oracle.c -- plain FP64 CPU oracle for the near-field direct sum.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
+ * includes this file; only the test suite, the package's smoke check and the
+ * CPU-baseline leg of the benchmark load it.  It shares no code, header or
+ * constant with the CUDA path.
+ *
+ * What it computes (Abacus near field, Section 2.1 and Section 4.3.1):
+ *   every particle i in cell c_i takes the force of every particle j in the
+ *   (2R+1)^3 cells whose index differs from c_i by at most R along each axis
+ *   (periodic), with the compact spline softening law
+ *       F(d) = [10 - 15 u + 6 u^2] d / eps^3      for r <  eps,  u = r/eps
+ *       F(d) = d / r^3                            for r >= eps
+ *   (Section 4.3.1, unnumbered equation), d = x_j - x_i, G m = 1.
+ *   The Plummer law of Eq. (eqn:plummer), F(d) = d / (r^2 + eps_p^2)^(3/2),
+ *   is available as the second softening mode.
+ *
+ * Everything is straight loops in double precision: sinks in parallel
+ * (OpenMP), each sink's 125 neighbour cells in (dx, dy, dz) order, each
+ * cell's particles in storage order, j == i included (d = 0 adds 0).
+ *
+ * Positions come in as cell-relative offsets in units of the cell width
+ * (the same values the GPU path holds, widened exactly to double).  The
+ * oracle converts every separation to box units, d = (x_j + Delta - x_i) w,
+ * and returns accelerations in box units.
+ *
+ * Parity of every function here is pinned by the CPU tests against closed
+ * forms, the C^2 spline derivation, brute force over all pairs, Newton's
+ * third law, lattice symmetry and finite differences.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#define SOFT_SPLINE 0
+#define SOFT_PLUMMER 1
+
+/* magnitude factor f(r) with F(d) = f(r) d  (Section 4.3.1 / Eq. eqn:plummer) */
+static double law_f(double r, double eps, int soft)
+{
+    if (soft == SOFT_PLUMMER) {
+        double s = r * r + eps * eps;
+        return 1.0 / (s * sqrt(s));
+    }
+    if (r < eps) {
+        double u = r / eps;
+        return (10.0 - 15.0 * u + 6.0 * u * u) / (eps * eps * eps);
+    }
+    return 1.0 / (r * r * r);
+}
+
+/* f'(r)/r, for the Jacobian J(d) = f I + (f'/r) d d^T.  At r = 0 the second
+ * term vanishes (it is f'(r) r dhat dhat^T), so 0 is returned there. */
+static double law_fprime_over_r(double r, double eps, int soft)
+{
+    if (r == 0.0) return 0.0;
+    if (soft == SOFT_PLUMMER) {
+        double s = r * r + eps * eps;
+        return -3.0 / (s * s * sqrt(s));
+    }
+    if (r < eps) {
+        double e3 = eps * eps * eps;
+        return (-15.0 / (eps * r) + 12.0 / (eps * eps)) / e3;
+    }
+    double r2 = r * r;
+    return -3.0 / (r2 * r2 * r);
+}
+
+static inline int64_t wrap(int64_t c, int64_t cpd)
+{
+    c %= cpd;
+    return c < 0 ? c + cpd : c;
+}
+
+double nf_oracle_law(double r, double eps, int soft) { return law_f(r, eps, soft) * r; }
+
+/*
+ * Near-field acceleration of a list of sinks.
+ *   cpd, R       : cells per dimension, near-field radius in cells
+ *   w, eps       : cell width and softening length, box units
+ *   cell_start   : int64[cpd^3 + 1]; particles of cell c are
+ *                  [cell_start[c], cell_start[c+1]) in storage order;
+ *                  cell id c = (cx cpd + cy) cpd + cz
+ *   xrel         : double[3 n], cell-relative positions in cell widths
+ *   sink, sink_cell : the sinks' storage indices and cell ids
+ *   acc          : double[3 nsink] out, box units
+ *   sumabs       : double[nsink] out (may be NULL): sum_j |F(d_ij)|
+ *   pairs        : int64 out (may be NULL): pair evaluations, j == i included
+ */
+void nf_oracle_forces(int64_t cpd, int R, double w, double eps, int soft,
+                      const int64_t *cell_start, const double *xrel,
+                      int64_t nsink, const int64_t *sink, const int64_t *sink_cell,
+                      double *acc, double *sumabs, int64_t *pairs)
+{
+    int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
+    for (int64_t s = 0; s < nsink; s++) {
+        int64_t i = sink[s];
+        int64_t c = sink_cell[s];
+        int64_t cz = c % cpd, cy = (c / cpd) % cpd, cx = c / (cpd * cpd);
+        double xi = xrel[3 * i], yi = xrel[3 * i + 1], zi = xrel[3 * i + 2];
+        double ax = 0.0, ay = 0.0, az = 0.0, sa = 0.0;
+        int64_t np_ = 0;
+        for (int dx = -R; dx <= R; dx++)
+            for (int dy = -R; dy <= R; dy++)
+                for (int dz = -R; dz <= R; dz++) {
+                    int64_t n = (wrap(cx + dx, cpd) * cpd + wrap(cy + dy, cpd)) * cpd + wrap(cz + dz, cpd);
+                    for (int64_t j = cell_start[n]; j < cell_start[n + 1]; j++) {
+                        double ddx = ((xrel[3 * j] + dx) - xi) * w;
+                        double ddy = ((xrel[3 * j + 1] + dy) - yi) * w;
+                        double ddz = ((xrel[3 * j + 2] + dz) - zi) * w;
+                        double r = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+                        double f = law_f(r, eps, soft);
+                        ax += f * ddx;
+                        ay += f * ddy;
+                        az += f * ddz;
+                        sa += f * r;
+                        np_++;
+                    }
+                }
+        acc[3 * s] = ax;
+        acc[3 * s + 1] = ay;
+        acc[3 * s + 2] = az;
+        if (sumabs) sumabs[s] = sa;
+        total += np_;
+    }
+    if (pairs) *pairs = total;
+}
+
+/*
+ * Brute force over all ordered pairs, written without cell lists: particle j
+ * acts on particle i through the one periodic image (shift n L, n in
+ * {-1,0,1}^3) whose cell lies at most R cells from i's cell along every axis,
+ * and not at all if there is none (Section 2.1: near field iff the cells are
+ * separated by at most R).  Separations are taken between global positions
+ * X = (c + 1/2 + x_rel) w.
+ *   cell_xyz : int64[3 n] integer cell coordinates of each particle
+ */
+void nf_oracle_bruteforce(int64_t cpd, int R, double w, double eps, int soft, int64_t n,
+                          const int64_t *cell_xyz, const double *xrel, double *acc)
+{
+    double L = w * (double)cpd;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; i++) {
+        double Xi[3], a[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 3; k++) Xi[k] = ((double)cell_xyz[3 * i + k] + 0.5 + xrel[3 * i + k]) * w;
+        for (int64_t j = 0; j < n; j++) {
+            double d[3];
+            int ok = 1;
+            for (int k = 0; k < 3 && ok; k++) {
+                int found = 0;
+                for (int s = -1; s <= 1; s++) {
+                    int64_t dc = cell_xyz[3 * j + k] + s * cpd - cell_xyz[3 * i + k];
+                    if (dc >= -R && dc <= R) {
+                        double Xj = ((double)cell_xyz[3 * j + k] + 0.5 + xrel[3 * j + k]) * w + s * L;
+                        d[k] = Xj - Xi[k];
+                        found = 1;
+                        break;
+                    }
+                }
+                ok = found;
+            }
+            if (!ok) continue;
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double f = law_f(r, eps, soft);
+            for (int k = 0; k < 3; k++) a[k] += f * d[k];
+        }
+        for (int k = 0; k < 3; k++) acc[3 * i + k] = a[k];
+    }
+}
+
+/*
+ * Adjoint of the near field: for a cotangent w_k (one 3-vector per
+ * particle, in storage order), the gradient of S = sum_i w_i . a_i with
+ * respect to the box-unit position of each listed sink k is
+ *     g_k = sum_{j in near(k)} J(d_kj) (w_j - w_k),   d_kj = x_j - x_k,
+ *     J(d) = f(r) I + (f'(r)/r) d d^T,
+ * with cell membership held fixed.  (From a_i = sum_j F(x_j - x_i): x_k
+ * enters a_k through every d_kj with sign -1 and every a_j, j near k,
+ * through d_jk with sign +1; J is even in d.)
+ */
+void nf_oracle_vjp(int64_t cpd, int R, double w, double eps, int soft,
+                   const int64_t *cell_start, const double *xrel, const double *wv,
+                   int64_t nsink, const int64_t *sink, const int64_t *sink_cell, double *grad)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t s = 0; s < nsink; s++) {
+        int64_t i = sink[s];
+        int64_t c = sink_cell[s];
+        int64_t cz = c % cpd, cy = (c / cpd) % cpd, cx = c / (cpd * cpd);
+        double xi = xrel[3 * i], yi = xrel[3 * i + 1], zi = xrel[3 * i + 2];
+        double g[3] = {0.0, 0.0, 0.0};
+        for (int dx = -R; dx <= R; dx++)
+            for (int dy = -R; dy <= R; dy++)
+                for (int dz = -R; dz <= R; dz++) {
+                    int64_t n = (wrap(cx + dx, cpd) * cpd + wrap(cy + dy, cpd)) * cpd + wrap(cz + dz, cpd);
+                    for (int64_t j = cell_start[n]; j < cell_start[n + 1]; j++) {
+                        double d[3];
+                        d[0] = ((xrel[3 * j] + dx) - xi) * w;
+                        d[1] = ((xrel[3 * j + 1] + dy) - yi) * w;
+                        d[2] = ((xrel[3 * j + 2] + dz) - zi) * w;
+                        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                        double f = law_f(r, eps, soft);
+                        double h = law_fprime_over_r(r, eps, soft);
+                        double dw[3];
+                        for (int k = 0; k < 3; k++) dw[k] = wv[3 * j + k] - wv[3 * i + k];
+                        double ddw = d[0] * dw[0] + d[1] * dw[1] + d[2] * dw[2];
+                        for (int k = 0; k < 3; k++) g[k] += f * dw[k] + h * ddw * d[k];
+                    }
+                }
+        for (int k = 0; k < 3; k++) grad[3 * s + k] = g[k];
+    }
+}

@@ -1,0 +1,79 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a private copy of the C oracle (on the CPU,
+in a temporary directory), points the oracle module at the mutant, and
+checks that at least one pin in test_oracle_pins fails.
+"""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "nf_oracle.c")
+
+FORCE_PINS = [
+    pins.test_spline_coefficients_from_c2_join,
+    pins.test_newtonian_tail_exact,
+    lambda: pins.test_two_body_newtonian(1.7),
+    lambda: pins.test_two_body_spline(0.5),
+    pins.test_no_force_beyond_near_field,
+    lambda: pins.test_cells_match_bruteforce(7, 900, "clustered"),
+    pins.test_third_law_total_force_vanishes,
+]
+VJP_PINS = [lambda: pins.test_vjp_matches_central_differences(0.01),
+            lambda: pins.test_vjp_matches_central_differences(0.08)]
+
+MUTANTS = [
+    ("spline coefficient", "(10.0 - 15.0 * u + 6.0 * u * u)", "(10.0 - 15.0 * u + 5.0 * u * u)", FORCE_PINS),
+    ("spline branch", "if (r < eps) {\n        double u", "if (r > eps) {\n        double u", FORCE_PINS),
+    ("separation sign", "double ddx = ((xrel[3 * j] + dx) - xi) * w;", "double ddx = (xi - (xrel[3 * j] + dx)) * w;",
+     FORCE_PINS),
+    ("missing neighbour layer", "for (int dz = -R; dz <= R; dz++) {\n                    int64_t n = (wrap(cx + dx, cpd) * cpd + wrap(cy + dy, cpd)) * cpd + wrap(cz + dz, cpd);\n                    for (int64_t j = cell_start[n]; j < cell_start[n + 1]; j++) {\n                        double ddx",
+     "for (int dz = -R; dz < R; dz++) {\n                    int64_t n = (wrap(cx + dx, cpd) * cpd + wrap(cy + dy, cpd)) * cpd + wrap(cz + dz, cpd);\n                    for (int64_t j = cell_start[n]; j < cell_start[n + 1]; j++) {\n                        double ddx",
+     FORCE_PINS),
+    ("no periodic wrap", "return c < 0 ? c + cpd : c;", "return c < 0 ? 0 : c;", FORCE_PINS),
+    ("cell unit dropped", "double ddz = ((xrel[3 * j + 2] + dz) - zi) * w;", "double ddz = ((xrel[3 * j + 2] + dz) - zi);",
+     FORCE_PINS),
+    ("transposed cell index", "int64_t cz = c % cpd, cy = (c / cpd) % cpd, cx = c / (cpd * cpd);\n        double xi = xrel[3 * i], yi = xrel[3 * i + 1], zi = xrel[3 * i + 2];\n        double ax",
+     "int64_t cx = c % cpd, cy = (c / cpd) % cpd, cz = c / (cpd * cpd);\n        double xi = xrel[3 * i], yi = xrel[3 * i + 1], zi = xrel[3 * i + 2];\n        double ax",
+     FORCE_PINS),
+    ("adjoint cotangent sign", "dw[k] = wv[3 * j + k] - wv[3 * i + k];", "dw[k] = wv[3 * j + k] + wv[3 * i + k];", VJP_PINS),
+    ("adjoint Jacobian term", "return -3.0 / (r2 * r2 * r);", "return 3.0 / (r2 * r2 * r);", VJP_PINS),
+    ("adjoint spline derivative", "(-15.0 / (eps * r) + 12.0 / (eps * eps))", "(-15.0 / (eps * r) + 6.0 / (eps * eps))",
+     VJP_PINS),
+]
+
+
+def _load_mutant(src_text, tmpdir):
+    path = os.path.join(tmpdir, "mutant.c")
+    so = os.path.join(tmpdir, "libmutant.so")
+    open(path, "w").write(src_text)
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, path, "-lm"])
+    lib = ctypes.CDLL(so)
+    ref = oracle.lib()
+    for name in ("nf_oracle_forces", "nf_oracle_bruteforce", "nf_oracle_vjp", "nf_oracle_law"):
+        getattr(lib, name).argtypes = getattr(ref, name).argtypes
+        getattr(lib, name).restype = getattr(ref, name).restype
+    return lib
+
+
+@pytest.mark.parametrize("name,old,new,checks", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(name, old, new, checks, monkeypatch):
+    text = open(SRC).read()
+    assert text.count(old) >= 1, f"mutation site for {name!r} not found"
+    mutated = text.replace(old, new, 1)
+    with tempfile.TemporaryDirectory() as tmp:
+        lib = _load_mutant(mutated, tmp)
+        monkeypatch.setattr(oracle, "_lib", lib)
+        failures = 0
+        for check in checks:
+            try:
+                check()
+            except AssertionError:
+                failures += 1
+        assert failures >= 1, f"no pin caught the mutant {name!r}"

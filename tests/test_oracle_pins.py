@@ -1,0 +1,341 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks it against a
+closed form, a derivation from a property the paper states, an independent
+brute-force code path, a symmetry, or finite differences.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import generators as gen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "spline_law.json")
+
+
+def _two_body(cpd, box, eps, X1, X2, soft=oracle.SPLINE):
+    b = oracle.bin_positions(np.array([X1, X2], dtype=np.float64), cpd, box)
+    acc = oracle.forces(b, eps, soft=soft)
+    Xq = oracle.global_positions(b)
+    # undo the sort so rows are (particle 1, particle 2)
+    inv = np.empty(2, dtype=np.int64)
+    inv[b.order] = np.arange(2)
+    return acc[inv], Xq[inv]
+
+
+def _min_image(d, box):
+    return d - box * np.round(d / box)
+
+
+# ------------------------------------------------------------------ pair law
+
+def test_spline_coefficients_from_c2_join():
+    """Section 4.3.1: F = (a + b u + c u^2) r/eps^3 joined to r^-2 with C^2 smoothness.
+
+    Solving the three join conditions reproduces the printed coefficients,
+    and the oracle's law matches the solved polynomial inside eps.
+    """
+    g = json.load(open(GOLDEN))
+    # F(u) eps^2 = a u + b u^2 + c u^3 ; at u = 1 match 1, -2, 6 (value, d/du, d2/du2 of u^-2)
+    A = np.array([[1.0, 1.0, 1.0], [1.0, 2.0, 3.0], [0.0, 2.0, 6.0]])
+    coef = np.linalg.solve(A, np.array([1.0, -2.0, 6.0]))
+    assert np.allclose(coef, g["spline_coefficients"], rtol=0, atol=1e-12)
+    for eps in (1e-3, 0.0078125, 0.37):
+        for u in np.linspace(0.0, 0.999, 37):
+            r = u * eps
+            expect = (coef[0] * u + coef[1] * u ** 2 + coef[2] * u ** 3) / eps ** 2
+            assert oracle.law(r, eps) == pytest.approx(expect, rel=1e-13, abs=1e-300)
+
+
+def test_newtonian_tail_exact():
+    """Beyond eps the law is exactly r/r^3 (|F| = 1/r^2)."""
+    eps = 0.01
+    for r in (0.01, 0.010000001, 0.02, 0.1, 0.7, 3.0):
+        assert oracle.law(r, eps) == pytest.approx(1.0 / r ** 2, rel=1e-15)
+
+
+def test_c2_continuity_numerical():
+    """Value, first and second derivative of |F(r)| agree on both sides of eps."""
+    eps = 0.05
+    h = 1e-4 * eps
+
+    def one_sided(sign):
+        rs = eps + sign * h * np.arange(0, 5)
+        f = np.array([oracle.law(r, eps) for r in rs])
+        # polynomial fit of degree 4 in (r - eps) on one side
+        p = np.polyfit(rs - eps, f, 4)
+        return p[-1], p[-2], 2 * p[-3]
+
+    lv, ld, ldd = one_sided(-1.0)
+    rv, rd, rdd = one_sided(+1.0)
+    assert lv == pytest.approx(1 / eps ** 2, rel=1e-9)
+    assert rv == pytest.approx(1 / eps ** 2, rel=1e-9)
+    assert ld == pytest.approx(-2 / eps ** 3, rel=1e-5)
+    assert rd == pytest.approx(-2 / eps ** 3, rel=1e-5)
+    assert ldd == pytest.approx(6 / eps ** 4, rel=2e-3)
+    assert rdd == pytest.approx(6 / eps ** 4, rel=2e-3)
+
+
+def test_plummer_is_gradient_of_plummer_potential():
+    """Eq. (eqn:plummer): |F| = -dPhi/dr with Phi = -1/sqrt(r^2 + eps^2)."""
+    eps = 0.02
+    for r in (1e-4, 0.01, 0.02, 0.05, 0.3):
+        h = 1e-6 * max(r, eps)
+        phi = lambda x: -1.0 / math.sqrt(x * x + eps * eps)
+        dphi = (phi(r + h) - phi(r - h)) / (2 * h)
+        assert oracle.law(r, eps, oracle.PLUMMER) == pytest.approx(dphi, rel=1e-7)
+
+
+def test_eps_conversion_matches_printed_factor():
+    """Section 4.3.1: equal minimum pairwise dynamical time gives eps_s = 2.16 eps_p.
+
+    The largest angular frequency^2 F(r)/r of each law (at r -> 0) is read off
+    the oracle; equating them gives the conversion factor.
+    """
+    g = json.load(open(GOLDEN))
+    r = 1e-9
+    w2_spline = oracle.law(r, 1.0, oracle.SPLINE) / r        # times eps_s^-3
+    w2_plummer = oracle.law(r, 1.0, oracle.PLUMMER) / r      # times eps_p^-3
+    ratio = (w2_spline / w2_plummer) ** (1.0 / 3.0)
+    assert ratio == pytest.approx(g["eps_s_over_eps_p"], rel=5e-3)
+
+
+# ------------------------------------------------------------------ two-body closed forms
+
+@pytest.mark.parametrize("sep_cells", [0.3, 0.9, 1.7, 2.4])
+def test_two_body_newtonian(sep_cells):
+    cpd, box = 5, 1.0
+    w = box / cpd
+    eps = 0.01 * w
+    direction = np.array([0.48, -0.6, 0.64])
+    X1 = np.array([0.5, 0.5, 0.5]) + 0.013
+    X2 = X1 + sep_cells * w * direction
+    acc, Xq = _two_body(cpd, box, eps, X1, X2)
+    d = _min_image(Xq[1] - Xq[0], box)
+    r = np.linalg.norm(d)
+    assert np.linalg.norm(acc[0]) == pytest.approx(1.0 / r ** 2, rel=1e-12)
+    assert np.allclose(acc[0], d / r ** 3, rtol=1e-12, atol=0)
+    assert np.array_equal(acc[0], -acc[1])
+
+
+@pytest.mark.parametrize("u", [0.0, 0.1, 0.5, 0.9, 0.999])
+def test_two_body_spline(u):
+    cpd, box = 7, 2.0
+    w = box / cpd
+    eps = 0.05 * w
+    X1 = np.array([1.0, 0.3, 1.9])
+    d0 = np.array([0.0, 0.6, 0.8]) * (u * eps)
+    acc, Xq = _two_body(cpd, box, eps, X1, X1 + d0)
+    d = _min_image(Xq[1] - Xq[0], box)
+    r = np.linalg.norm(d)
+    uu = r / eps
+    expect = (10 * uu ** 3 - 15 * uu ** 4 + 6 * uu ** 5) / r ** 2 if r > 0 else 0.0
+    assert np.linalg.norm(acc[0]) == pytest.approx(expect, rel=1e-11, abs=1e-300)
+    assert np.array_equal(acc[0], -acc[1])
+
+
+def test_no_force_beyond_near_field():
+    """Particles more than R cells apart (per axis) do not interact in the near field."""
+    cpd, box = 9, 1.0
+    w = box / cpd
+    X1 = np.array([0.5, 0.5, 0.5]) * w + np.array([4, 4, 4]) * w
+    far = X1 + np.array([3.0, 0.0, 0.0]) * w
+    acc, _ = _two_body(cpd, box, 1e-3, X1, far)
+    assert np.all(acc == 0.0)
+    near = X1 + np.array([2.0, -2.0, 2.0]) * w
+    acc, _ = _two_body(cpd, box, 1e-3, X1, near)
+    assert np.all(np.abs(acc) > 0)
+
+
+# ------------------------------------------------------------------ brute force & symmetry
+
+@pytest.mark.parametrize("cpd,n,kind", [(5, 300, "uniform"), (6, 500, "uniform"), (7, 900, "clustered"),
+                                        (5, 400, "clustered")])
+def test_cells_match_bruteforce(cpd, n, kind):
+    rng = np.random.default_rng(cpd * 1000 + n)
+    if kind == "uniform":
+        X = rng.random((n, 3))
+    else:
+        X, _ = gen.clustered(n, rng, 3, 0.3 / cpd, 1.0 / cpd)
+    eps = 0.02 / cpd
+    b = oracle.bin_positions(X, cpd)
+    a_cells = oracle.forces(b, eps)
+    a_brute = oracle.bruteforce(b, eps)
+    scale = np.abs(a_brute).max()
+    assert np.abs(a_cells - a_brute).max() <= 1e-12 * scale
+
+
+def test_third_law_total_force_vanishes():
+    rng = np.random.default_rng(3)
+    X, _ = gen.clustered(4000, rng, 4, 0.05, 0.2)
+    b = oracle.bin_positions(X, 8)
+    acc, sa, _ = oracle.forces(b, 2e-3, with_sumabs=True)
+    assert np.abs(acc.sum(axis=0)).max() <= 1e-13 * sa.sum()
+
+
+def test_lattice_forces_vanish():
+    """Section 2.1 lattice test: the same offset in every cell gives zero near force."""
+    cpd = 7
+    w = 1.0 / cpd
+    g = (np.arange(cpd) + 0.5) * w
+    X = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3) + np.array([0.1, -0.2, 0.3]) * w
+    b = oracle.bin_positions(X, cpd)
+    acc, sa, _ = oracle.forces(b, 0.01 * w, with_sumabs=True)
+    assert np.abs(acc).max() <= 1e-14 * sa.max()
+
+
+def test_whole_cell_translation_permutes_forces_exactly():
+    rng = np.random.default_rng(7)
+    cpd = 6
+    X, _ = gen.clustered(1500, rng, 3, 0.1, 0.3)
+    b = oracle.bin_positions(X, cpd)
+    a0 = oracle.forces(b, 1e-3)
+    xyz = b.cell_xyz()
+    shifted = (xyz + np.array([2, 5, 1])) % cpd
+    cell2 = (shifted[:, 0] * cpd + shifted[:, 1]) * cpd + shifted[:, 2]
+    order = np.argsort(cell2, kind="stable")
+    counts = np.bincount(cell2, minlength=cpd ** 3)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    b2 = oracle.from_sorted(cpd, 1.0, off, b.xq[order])
+    a1 = oracle.forces(b2, 1e-3)
+    assert np.array_equal(a1, a0[order])
+
+
+def test_pair_count_two_ways():
+    rng = np.random.default_rng(11)
+    X, _ = gen.clustered(3000, rng, 3, 0.05, 0.2)
+    b = oracle.bin_positions(X, 7)
+    _, _, pairs = oracle.forces(b, 1e-3, with_sumabs=True)
+    assert pairs == oracle.pair_count(b)
+    b5 = oracle.bin_positions(X[:700], 5)
+    assert oracle.pair_count(b5) == 700 * 700          # every pair is near at cpd = 2R+1
+
+
+# ------------------------------------------------------------------ binning
+
+def _bin_python(X, cpd, box):
+    """Per-particle pure-Python restatement of the binning rule (small inputs)."""
+    inv_w = float(cpd) / float(box)
+    rows = []
+    for idx, p in enumerate(X.tolist()):
+        cxyz, rel = [], []
+        for v in p:
+            s = v * inv_w
+            c = math.floor(s)
+            rel.append(round(((s - c) - 0.5) * 2 ** 22) / 2 ** 22)   # Python round: half to even
+            cxyz.append(c % cpd)
+        cell = (cxyz[0] * cpd + cxyz[1]) * cpd + cxyz[2]
+        rows.append((cell, idx, rel))
+    rows.sort(key=lambda t: (t[0], t[1]))
+    return rows
+
+
+def test_binning_matches_python_restatement():
+    rng = np.random.default_rng(5)
+    cpd, box = 5, 1.0
+    X = rng.random((400, 3))
+    X[:20] = np.floor(X[:20] * cpd) / cpd            # exactly on cell faces
+    X[20:25] = np.nextafter(1.0, 0.0)                # just below the box edge
+    X[25:30] = -1e-3                                 # outside, wraps
+    X[30:35] = 1.0 + 1e-3                            # outside, wraps
+    X[35:60] = X[35]                                 # many in one cell: stability
+    b = oracle.bin_positions(X, cpd, box)
+    rows = _bin_python(X, cpd, box)
+    assert b.cell.tolist() == [r[0] for r in rows]
+    assert b.order.tolist() == [r[1] for r in rows]
+    assert np.array_equal(b.xq.astype(np.float64), np.array([r[2] for r in rows]))
+    assert int(b.offsets[-1]) == 400 and np.array_equal(np.diff(b.offsets), b.counts)
+    assert np.all(np.abs(b.xq) <= 0.5)
+
+
+def test_quantised_offsets_make_fp32_separations_exact():
+    """With x on the 2^-22 grid, (x_j + D) - x_i is exact in FP32 for |D| <= 2."""
+    rng = np.random.default_rng(9)
+    xi = oracle.quantise(rng.uniform(-0.5, 0.5, 20000))
+    xj = oracle.quantise(rng.uniform(-0.5, 0.5, 20000))
+    for D in (-2, -1, 0, 1, 2):
+        f32 = (xj + np.float32(D)) - xi
+        f64 = (xj.astype(np.float64) + D) - xi.astype(np.float64)
+        assert np.array_equal(f32.astype(np.float64), f64)
+
+
+# ------------------------------------------------------------------ adjoint
+
+@pytest.mark.parametrize("eps", [0.01, 0.08])
+def test_vjp_matches_central_differences(eps):
+    """eps = 0.08 puts most close pairs inside the spline, 0.01 most outside."""
+    rng = np.random.default_rng(13)
+    cpd = 6
+    X, _ = gen.clustered(800, rng, 2, 0.05, 0.15)
+    b = oracle.bin_positions(X, cpd)
+    wv = gen.cotangent(b.n, rng)
+    g = oracle.vjp(b, eps, wv)
+    x64 = b.xq.astype(np.float64)
+    h = 1e-3 * eps
+    for k in rng.choice(b.n, 12, replace=False):
+        for ax in range(3):
+            vals = []
+            for sgn in (+1, -1):
+                xp = x64.copy()
+                xp[k, ax] += sgn * h / b.w
+                bp = oracle.Binned(b.cpd, b.box, b.order, b.cell, xp, b.offsets, b.counts)
+                vals.append(float((oracle.forces(bp, eps) * wv).sum()))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert fd == pytest.approx(g[k, ax], rel=2e-5, abs=1e-6 * np.abs(g).max())
+
+
+# ------------------------------------------------------------------ kick / drift
+
+def test_drift_without_force_is_exact():
+    X = np.array([[0.1, 0.2, 0.3], [0.95, 0.5, 0.01]])
+    V = np.array([[0.25, -0.5, 0.125], [0.5, 0.0, -0.25]])
+    X1, V1 = oracle.kick_drift(X, V, np.zeros_like(X), 0.125, 1.0)
+    assert np.array_equal(V1, V)
+    assert np.array_equal(X1, np.mod(X + V * 0.125, 1.0))
+
+
+def test_two_body_circular_orbit_closes_at_second_order():
+    """Leapfrog on a near-field two-body circular orbit: phase error ~ dt^2."""
+    cpd, box = 5, 1.0
+    eps = 1e-3
+    r = 0.1
+    vrel = math.sqrt(2.0 / r)            # equal unit masses, G m = 1: |a_rel| = 2/r^2
+    period = 2 * math.pi * r / vrel
+
+    def run(nsteps):
+        dt = period / nsteps
+        X = np.array([[0.5 - r / 2, 0.5, 0.5], [0.5 + r / 2, 0.5, 0.5]])
+        V = np.array([[0.0, -vrel / 2, 0.0], [0.0, vrel / 2, 0.0]])
+
+        def acc_of(X):
+            b = oracle.bin_positions(X, cpd, box)
+            a = np.empty((2, 3))
+            a[b.order] = oracle.forces(b, eps)
+            return a
+
+        A = acc_of(X)
+        V = V - 0.5 * dt * A            # leapfrog: velocities at half steps
+        for _ in range(nsteps):
+            A = acc_of(X)
+            X, V = oracle.kick_drift(X, V, A, dt, box)
+        return np.linalg.norm(X[1] - X[0] - np.array([r, 0.0, 0.0]))
+
+    e1, e2 = run(200), run(400)
+    assert e1 < 0.05 * r
+    assert 3.0 < e1 / e2 < 5.0
+
+
+# ------------------------------------------------------------------ error statistics
+
+def test_error_stats_definitions():
+    ref = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0], [0.0, 0.0, 4.0]])
+    test = ref + np.array([[1e-6, 0, 0], [0, 0, 0], [0, 0, 4e-3]])
+    s = oracle.error_stats(test, ref, sumabs=np.array([1.0, 1.0, 1.0]))
+    assert s["rms_rel"] == pytest.approx(math.sqrt((1e-12 + 16e-6) / 21.0))
+    assert s["median"] == pytest.approx(1e-6)
+    assert s["frac_gt_1e-4"] == pytest.approx(1 / 3)
+    assert s["max_bound_ratio"] == pytest.approx(4e-3 * 2 ** 24)
