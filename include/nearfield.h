@@ -1,0 +1,214 @@
+/*
+ * nearfield.h -- C ABI of the B300 near-field direct-sum library.
+ *
+ * The library computes the near-field force of the Abacus N-body method
+ * (Garrison, Eisenstein & Pinto, arXiv:1810.02916, Section 2.1): the
+ * periodic box is cut into cpd^3 cubic cells, every particle belongs to one
+ * cell, and every particle takes the softened Newtonian force of every
+ * particle in the (2R+1)^3 cells whose index differs from its own by at most
+ * R along each axis (periodic).  The pair law is the compact spline of
+ * Section 4.3.1,
+ *     F(d) = [10 - 15 u + 6 u^2] d / eps^3   (r < eps, u = r / eps)
+ *     F(d) = d / r^3                         (r >= eps),
+ * with d = x_j - x_i and G m = 1 (the caller scales by G m).  Positions are
+ * stored as offsets from the owning cell's centre (Section 2.1, last
+ * paragraph), in units of the cell width w = box / cpd.
+ *
+ * Conventions for every entry point:
+ *  - Return value: an nf_status code.  Nothing aborts the process.  On an
+ *    error the box keeps its previous state unless stated otherwise, and
+ *    nf_last_error() returns a one-line message.
+ *  - Pointers are plain host or device pointers (CUDA unified addressing
+ *    tells them apart); the caller owns them and the library copies from or
+ *    into them.  Host pointers may be pageable or pinned; pinned ones make
+ *    the copies asynchronous on the box's stream.
+ *  - All device work is enqueued on the box's stream (nf_set_stream, default
+ *    the legacy default stream).  Entry points marked (async) do not wait
+ *    for the GPU when their outputs are device pointers; device faults then
+ *    surface at the next call that synchronises.
+ *  - Particle arrays are in the library's storage order: sorted by cell id
+ *    c = (cx cpd + cy) cpd + cz (x-major, z fastest), then by particle id
+ *    within the cell (see nf_bin_particles).
+ */
+#ifndef NEARFIELD_H
+#define NEARFIELD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nf_box nf_t;
+
+enum nf_status {
+    NF_OK = 0,
+    NF_EINVAL = 1,   /* bad argument or input data */
+    NF_ENOMEM = 2,   /* device or host allocation failed */
+    NF_ECUDA = 3,    /* a CUDA call failed (message in nf_last_error) */
+    NF_ETIMEOUT = 4, /* a bounded device-side wait ran out */
+    NF_ESTATE = 5    /* call not valid in the box's current state */
+};
+
+/* Accumulation of the per-sink force sums (nf_set_accumulation). */
+enum nf_accumulation {
+    NF_ACC_COMPENSATED = 0, /* FP32 partials over blocks of sources, folded with an
+                               exact two-sum into (hi, lo), reduced in FP64 (default) */
+    NF_ACC_PLAIN = 1        /* one FP32 running sum per sink (the plain FP32 kernel) */
+};
+
+/*
+ * nf_create -- make an empty box.
+ *   cpd  cells per dimension (K in Section 2.1), cpd >= 2R+1 so that no cell
+ *        appears twice in a neighbourhood, cpd^3 < 2^31
+ *   R    near-field radius in cells (Section 2.1; the paper uses 2).  This
+ *        build supports R = 2 only.
+ *   eps  spline softening length eps_s in box units, 0 < eps < box/cpd (the
+ *        spline must close inside the near field)
+ *   box  box side length, > 0
+ * Errors: NF_EINVAL for any violated bound, NF_ENOMEM, NF_ECUDA.
+ * The box owns all of its device buffers; nf_destroy frees them.
+ */
+int nf_create(int cpd, int R, double eps, double box, nf_t **out);
+
+/* nf_destroy -- free the box and its device memory (NULL is a no-op). */
+void nf_destroy(nf_t *nf);
+
+/* nf_last_error -- message of the last failed call on this box ("" if none).
+ * With nf == NULL, the message of the last failed nf_create. */
+const char *nf_last_error(const nf_t *nf);
+
+/* nf_set_stream -- enqueue all later work of this box on `stream`
+ * (a cudaStream_t; NULL = legacy default stream). */
+int nf_set_stream(nf_t *nf, void *stream);
+
+/* nf_set_accumulation -- NF_ACC_COMPENSATED (default) or NF_ACC_PLAIN. */
+int nf_set_accumulation(nf_t *nf, int mode);
+
+/*
+ * nf_bin_particles -- load particles from global positions (device binning).
+ *   xyz  n x 3 doubles, box units, any finite values (wrapped periodically);
+ *        host or device pointer, particle id = row index
+ *   n    number of particles, 0 <= n < 2^31
+ * Each particle gets the cell c = floor(x cpd / box) per axis (wrapped) and
+ * the offset x_rel = (x cpd / box - c) - 1/2 in cell widths, rounded to a
+ * multiple of 2^-22 (half to even).  Particles are sorted by cell id, stably
+ * in id order.  Velocities are reset to zero.  NF_EINVAL for non-finite
+ * positions.  Section 2.1 (cells, cell-centred positions).  Synchronises.
+ */
+int nf_bin_particles(nf_t *nf, const double *xyz, int64_t n);
+
+/*
+ * nf_set_particles -- load particles that the caller has already binned.
+ *   cell_offsets  cpd^3 + 1 int64, cell_offsets[c] = first particle of cell c
+ *   counts        cpd^3 int32, particles per cell
+ *   pos           n x 4 floats (x, y, z, ignored), cell-relative offsets in
+ *                 cell widths, sorted by cell; |x| <= 1/2 (1 + 2^-20)
+ *   n             number of particles
+ * Offsets are rounded to multiples of 2^-22 cell widths (half to even).
+ * Validated on the device: counts >= 0, sum(counts) = n, cell_offsets is the
+ * exclusive scan of counts, offsets finite and within bounds; NF_EINVAL
+ * otherwise (state unchanged).  Particle ids are the storage indices.
+ * Velocities are reset to zero.  Synchronises.
+ */
+int nf_set_particles(nf_t *nf, const int64_t *cell_offsets, const int32_t *counts,
+                     const float *pos, int64_t n);
+
+/* nf_set_velocities -- n x 4 floats (vx, vy, vz, ignored), box units per
+ * unit time, storage order.  (async) */
+int nf_set_velocities(nf_t *nf, const float *vel);
+
+/*
+ * nf_get_particles -- read the state back (checkpoint).  Any output may be
+ * NULL.  cell_offsets: cpd^3 + 1 int64; counts: cpd^3 int32; pos, vel:
+ * n x 4 floats as in nf_set_particles / nf_set_velocities; perm: n int64,
+ * perm[k] = id of the particle stored at k.  Synchronises.
+ */
+int nf_get_particles(nf_t *nf, int64_t *cell_offsets, int32_t *counts, float *pos,
+                     float *vel, int64_t *perm);
+
+/* nf_num_particles -- number of particles held by the box. */
+int nf_num_particles(const nf_t *nf, int64_t *n);
+
+/*
+ * nf_pair_count -- number of ordered (sink, source) evaluations one force
+ * pass makes: sum over cells of n_c times the particle count of its
+ * (2R+1)^3 neighbourhood (self pairs included).  Synchronises.
+ */
+int nf_pair_count(nf_t *nf, int64_t *pairs);
+
+/*
+ * nf_forces -- near-field accelerations (Section 2.1, Section 4.3.1).
+ *   acc  n x 4 floats (ax, ay, az, 0), box units, storage order; host or
+ *        device pointer, or NULL to keep the result inside the box only
+ * The FP64 per-sink sums are kept in the box (nf_get_forces64) and feed
+ * nf_kick_drift.  (async for device or NULL acc)
+ */
+int nf_forces(nf_t *nf, float *acc);
+
+/* nf_get_forces64 -- the FP64 sums of the last nf_forces, n x 3 doubles in
+ * box units, storage order.  (async for device acc) */
+int nf_get_forces64(nf_t *nf, double *acc);
+
+/*
+ * nf_kick_drift -- one leapfrog kick and drift in FP64 arithmetic (Table 1,
+ * rows Kick and Drift): v += a dt with a from the last nf_forces, then
+ * x += v dt; positions are re-binned (new cells, offsets rounded to the
+ * 2^-22 grid, stable sort by cell in id order).  Velocities and offsets are
+ * stored as FP32.  If any particle would move more than 0.8 cell widths
+ * along an axis (the drift limit of Section 4.2.1) nothing is changed and
+ * NF_EINVAL is returned.  NF_ESTATE without a previous nf_forces.
+ * Synchronises.
+ */
+int nf_kick_drift(nf_t *nf, double dt);
+
+/*
+ * nf_vjp -- adjoint (vector-Jacobian product) of the accelerations.
+ *   w     n x 4 floats (cotangent w_k, storage order; 4th ignored)
+ *   grad  n x 4 floats out: d(sum_i w_i . a_i)/dx_k in box units
+ *         = sum_{j near k} J(x_j - x_k) (w_j - w_k),
+ *         J(d) = f(r) I + (f'(r)/r) d d^T, F(d) = f(r) d,
+ *         with cell membership held fixed.
+ * The paper has no adjoint; this differentiates its pair law (Section
+ * 4.3.1).  (async for device grad)
+ */
+int nf_vjp(nf_t *nf, const float *w, float *grad);
+
+/*
+ * nf_forces_batched -- near-field accelerations of several independent
+ * boxes in one persistent launch from one device work queue.
+ *   boxes  nbox box handles (all with particles loaded), 1 <= nbox <= 4096
+ *   acc    nbox output pointers as in nf_forces (entries may be NULL)
+ * Work runs on the first box's stream.  The batch's combined work list is
+ * rebuilt when the set of boxes or a box's particles changed since the last
+ * call; otherwise the call enqueues only a queue reset and one kernel (plus
+ * output copies for host outputs), allocates nothing and does not
+ * synchronise.
+ */
+int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc);
+
+/*
+ * nf_profile -- timing of the pair kernel.  With enable = 1, later
+ * nf_forces / nf_forces_batched / nf_vjp calls bracket the pair kernel with
+ * CUDA events on the box's stream; nf_profile_read returns the number of
+ * timed launches and their summed duration in milliseconds (synchronises)
+ * and resets both.
+ */
+int nf_profile(nf_t *nf, int enable);
+int nf_profile_read(nf_t *nf, int64_t *launches, double *ms);
+
+/*
+ * nf_set_shape / nf_tune -- launch shape of the pair kernel: warps per block
+ * (1..8) and sources staged per round (128 or 256).  nf_tune times every
+ * candidate on this machine's particles (a few pair passes), keeps the fastest
+ * and caches it per device and occupancy signature for later boxes;
+ * report (may be NULL) receives a one-line summary.  Synchronises.
+ */
+int nf_set_shape(nf_t *nf, int warps, int stage);
+int nf_tune(nf_t *nf, char *report, int report_len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEARFIELD_H */

@@ -1,0 +1,89 @@
+// nf_internal.cuh -- shared declarations of the library's translation units.
+// Not part of the public ABI (include/nearfield.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nf {
+
+// Near-field radius supported by the kernels (Section 2.1: R = 2, 125 cells).
+constexpr int kR = 2;
+constexpr int kNbr = (2 * kR + 1) * (2 * kR + 1) * (2 * kR + 1);   // 125
+constexpr int kTile = 128;                                            // sinks per work item (max)
+
+// One box as the kernels see it.
+struct BoxDev {
+    const float4 *pos;        // n, cell-relative offsets (cell widths), sorted by cell
+    const int *cell_start;    // cpd^3 + 1
+    float4 *acc_out;          // n, FP32 output in box units (may be null)
+    double *acc64;            // 3 n, FP64 output in box units (may be null)
+    const float4 *cot;        // n, cotangent for the adjoint (null for forces)
+    int cpd;
+    int n;
+    float a0, a1, a2;         // spline g(r) = a0 + a1 r + a2 r^2 in cell units
+    float eps2;               // eps^2 in cell units (adjoint branch test)
+    double acc_scale;         // (cpd / box)^2: cell-unit acceleration -> box units
+    double grad_scale;        // (cpd / box)^3: cell-unit Jacobian -> box units
+};
+
+// A work item: up to kTile sinks of one cell against its whole neighbourhood.
+struct Item {
+    int box;
+    int cell;
+    int sink_begin;
+    int sink_count;
+};
+
+// Occupancy classes used to order the work queue (largest cells first).
+constexpr int kClasses = 5;
+__host__ __device__ inline int occupancy_class(int n)
+{
+    return n >= 4096 ? 0 : n >= 512 ? 1 : n >= 64 ? 2 : n >= 8 ? 3 : 4;
+}
+
+// Launch shape of the pair kernel.
+struct PairShape {
+    int warps;      // warps per block (1..8)
+    int stage;      // sources staged per round (128 or 256)
+    int blocks;     // persistent grid size (0 = fill the GPU)
+};
+
+// ---- pair kernel (nf_pair.cu) ----
+cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, int compensated,
+                        int adjoint, PairShape shape, int sm_count, cudaStream_t st);
+int pair_max_blocks_per_sm(int compensated, int adjoint, PairShape shape);
+
+// ---- scan / sort / binning (nf_sort.cu) ----
+size_t scan_temp_bytes(int64_t n);
+cudaError_t exclusive_scan_i32(const int *in, int *out, int64_t n, void *temp, cudaStream_t st);
+size_t radix_temp_bytes(int64_t n);
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, int64_t n,
+                             int key_bits, void *temp, int *result_in_alt, cudaStream_t st);
+cudaError_t bin_global(const double *xyz, int n, int cpd, double inv_w, uint32_t *key, uint32_t *val,
+                       float4 *xq_by_id, int *counts, int *err, cudaStream_t st);
+cudaError_t gather_sorted(const uint32_t *perm, const float4 *xq_by_id, const float4 *vel_by_id, float4 *pos,
+                          float4 *vel, int n, cudaStream_t st);
+cudaError_t validate_loaded(const int64_t *offsets, const int32_t *counts, const float4 *pos, int ncell, int n,
+                            int *cell_start, float4 *pos_out, int *err, cudaStream_t st);
+cudaError_t fill_cell_ids(const int *cell_start, int ncell, int n, uint32_t *cell_of, cudaStream_t st);
+cudaError_t iota_u32(uint32_t *p, int n, cudaStream_t st);
+cudaError_t count_keys(const uint32_t *keys, int n, int *counts, cudaStream_t st);
+
+// ---- planner (nf_plan.cu) ----
+// Items of one box and one occupancy class, appended at items[*n_items]
+// (*n_items is a device int and is advanced).
+cudaError_t plan_items_class(const int *cell_start, int ncell, int box_index, int cls, Item *items, int *n_items,
+                             int *scratch_counts, int *scratch_offsets, void *scan_temp, cudaStream_t st);
+cudaError_t zero_device_int(int *p, cudaStream_t st);
+cudaError_t neighbour_pairs(const int *cell_start, int cpd, unsigned long long *pairs, int *tmp_a, int *tmp_b,
+                            cudaStream_t st);
+
+// ---- kick / drift (nf_step.cu) ----
+cudaError_t kick(const float4 *vel, const double *acc64, double dt, double inv_w, int n, float4 *vel_new,
+                 int *cap_violations, cudaStream_t st);
+cudaError_t drift(const float4 *pos, const float4 *vel_new, const uint32_t *cell_of, const uint32_t *perm,
+                  double dt, double inv_w, int cpd, int n, uint32_t *key_by_id, uint32_t *val_by_id,
+                  float4 *xq_by_id, float4 *vel_by_id, cudaStream_t st);
+
+}  // namespace nf

@@ -1,0 +1,462 @@
+// nf_pair.cu -- the near-field pair kernel (forces and adjoint).
+//
+// Work: every particle i of a cell takes F(x_j - x_i) from every particle j of
+// the 125 cells within R = 2 cells of its own (Section 2.1), with the spline
+// law of Section 4.3.1 written branch-free as f = min(r^-3, g(r)),
+// g(r) = (10 - 15 r/eps + 6 r^2/eps^2) / eps^3.  The two agree for every
+// r > 0: r^3 g(r) = 10u^3 - 15u^4 + 6u^5 (u = r/eps) rises monotonically
+// (derivative 30u^2 (1-u)^2) through 1 at u = 1, so g <= r^-3 exactly when
+// r <= eps; this is the single `min` of the paper's footnote to Section 4.3.1.
+//
+// Structure (one persistent grid, one warp per work item):
+//   * a work item is up to 128 sinks of one cell; the warp pulls item indices
+//     from a device queue (atomic counter), largest cells first;
+//   * the warp builds a 125-entry table of its neighbour cells (start, prefix
+//     of counts) in shared memory;
+//   * sources are streamed in rounds of B particles: each lane gathers B/32
+//     float4 with cp.async (16 B each, coalesced along each cell's run) into
+//     one of two per-warp shared-memory buffers while the previous round is
+//     being computed; once landed, each lane adds its own entries' integer
+//     cell offset (dx, dy, dz), so every source is in the sink cell's frame;
+//   * sinks live in registers: with > 16 sinks every lane holds S = 1, 2 or 4
+//     sinks and reads each staged source as a shared-memory broadcast; with
+//     <= 16 sinks the lanes split the sources between them (each sink owns
+//     32/P lanes, P = sinks rounded up to a power of two) and the partial
+//     sums are combined with a fixed xor-shuffle tree;
+//   * pair arithmetic is FP32: rsqrt on the SFU plus one Newton step, 20 FP32
+//     pipe operations per pair;
+//   * accumulation: plain FFMA within a round (<= B sources), folded after
+//     every round into a (hi, lo) pair with an exact two-sum and reduced to
+//     FP64 per sink at the end (compensated mode); or one FP32 running sum
+//     per sink (plain mode).
+//
+// Exactness of separations: offsets are multiples of 2^-22 cell widths with
+// |x| <= 1/2, so x_j + D (|D| <= 2) and (x_j + D) - x_i are exact in FP32.
+// Every item owns its sinks and sums its sources in a fixed order, so the
+// result does not depend on which warp ran which item (bit-reproducible).
+#include <cfloat>
+
+#include "nf_internal.cuh"
+
+namespace nf {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kFar = 1.0e18f;   // padding source: y^3 underflows to 0, contributes exactly zero
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// exact sum a + b = s + e (two-sum; no FMA involved)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+struct Comp3 {
+    float hx, hy, hz;   // running high parts
+    float lx, ly, lz;   // accumulated low parts
+};
+
+__device__ __forceinline__ void comp_init(Comp3 &c) { c.hx = c.hy = c.hz = c.lx = c.ly = c.lz = 0.f; }
+
+__device__ __forceinline__ void comp_fold(Comp3 &c, float &px, float &py, float &pz)
+{
+    float s, e;
+    two_sum(c.hx, px, s, e); c.hx = s; c.lx = __fadd_rn(c.lx, e);
+    two_sum(c.hy, py, s, e); c.hy = s; c.ly = __fadd_rn(c.ly, e);
+    two_sum(c.hz, pz, s, e); c.hz = s; c.lz = __fadd_rn(c.lz, e);
+    px = py = pz = 0.f;
+}
+
+// combine with the partner lane `o` (xor); both lanes end with the same value
+__device__ __forceinline__ void comp_xor_combine(Comp3 &c, int o)
+{
+    float s, e;
+    float h2 = __shfl_xor_sync(kFull, c.hx, o), l2 = __shfl_xor_sync(kFull, c.lx, o);
+    two_sum(c.hx, h2, s, e); c.hx = s; c.lx = __fadd_rn(__fadd_rn(c.lx, l2), e);
+    h2 = __shfl_xor_sync(kFull, c.hy, o); l2 = __shfl_xor_sync(kFull, c.ly, o);
+    two_sum(c.hy, h2, s, e); c.hy = s; c.ly = __fadd_rn(__fadd_rn(c.ly, l2), e);
+    h2 = __shfl_xor_sync(kFull, c.hz, o); l2 = __shfl_xor_sync(kFull, c.lz, o);
+    two_sum(c.hz, h2, s, e); c.hz = s; c.lz = __fadd_rn(__fadd_rn(c.lz, l2), e);
+}
+
+// one pair: a += f(r) d with f = min(r^-3, a0 + a1 r + a2 r^2)
+__device__ __forceinline__ void pair_force(const float4 q, float xi, float yi, float zi, float &ax, float &ay,
+                                           float &az, float a0, float a1, float a2)
+{
+    const float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
+    float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    r2 = fmaxf(r2, FLT_MIN);                 // r = 0 (self pair): finite g, times d = 0
+    float y = rsqrtf(r2);                    // SFU
+    const float t = r2 * y;
+    const float h = t * y;
+    const float e = fmaf(h, -0.5f, 0.5f);
+    y = fmaf(y, e, y);                       // one Newton step for r2^-1/2
+    const float r = fmaf(t, e, t);           // r2 * y
+    const float y3 = y * y * y;
+    const float g = fmaf(fmaf(a2, r, a1), r, a0);
+    const float f = fminf(y3, g);
+    ax = fmaf(f, dx, ax);
+    ay = fmaf(f, dy, ay);
+    az = fmaf(f, dz, az);
+}
+
+// one pair of the adjoint: grad += J(d) (w_j - w_k), J = f I + (f'/r) d d^T
+__device__ __forceinline__ void pair_adjoint(const float4 q, const float4 wj, float xi, float yi, float zi, float wx,
+                                             float wy, float wz, float &gx, float &gy, float &gz, float a0, float a1,
+                                             float a2, float eps2)
+{
+    const float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
+    float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const bool inside = r2 < eps2;
+    r2 = fmaxf(r2, FLT_MIN);
+    float y = rsqrtf(r2);
+    const float t = r2 * y;
+    const float h = t * y;
+    const float e = fmaf(h, -0.5f, 0.5f);
+    y = fmaf(y, e, y);
+    const float r = fmaf(t, e, t);
+    const float y2 = y * y;
+    const float y3 = y2 * y;
+    // spline: f = a0 + a1 r + a2 r^2, f'/r = a1 / r + 2 a2 ; Newtonian: f = r^-3, f'/r = -3 r^-5
+    const float f = inside ? fmaf(fmaf(a2, r, a1), r, a0) : y3;
+    const float hh = inside ? fmaf(a1, y, 2.f * a2) : -3.f * y3 * y2;
+    const float ux = wj.x - wx, uy = wj.y - wy, uz = wj.z - wz;
+    const float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
+    const float hd = hh * du;
+    gx = fmaf(hd, dx, fmaf(f, ux, gx));
+    gy = fmaf(hd, dy, fmaf(f, uy, gy));
+    gz = fmaf(hd, dz, fmaf(f, uz, gz));
+}
+
+// 125-entry neighbour table of `cell`: tstart[t] = first particle, tpre[t] =
+// exclusive prefix of counts, tpre[125] = total.  t = (dx+2)*25 + (dy+2)*5 + (dz+2).
+__device__ __forceinline__ int build_table(const BoxDev &bx, int cell, int *tstart, int *tpre, int lane)
+{
+    const int C = bx.cpd;
+    const int cz = cell % C, cy = (cell / C) % C, cx = cell / (C * C);
+    int cnt[4];
+    int local = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int t = 4 * lane + u;
+        int c = 0;
+        if (t < kNbr) {
+            int nx = cx + t / 25 - 2, ny = cy + (t / 5) % 5 - 2, nz = cz + t % 5 - 2;
+            nx += nx < 0 ? C : 0; nx -= nx >= C ? C : 0;
+            ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
+            nz += nz < 0 ? C : 0; nz -= nz >= C ? C : 0;
+            const int n = (nx * C + ny) * C + nz;
+            const int s0 = __ldg(bx.cell_start + n);
+            c = __ldg(bx.cell_start + n + 1) - s0;
+            tstart[t] = s0;
+        }
+        cnt[u] = c;
+        local += c;
+    }
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int run = incl - local;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int t = 4 * lane + u;
+        if (t <= kNbr) tpre[t] = run;
+        run += cnt[u];
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    __syncwarp();
+    return total;
+}
+
+// neighbour-table slot of flat source index f: tpre[t] <= f < tpre[t+1]
+__device__ __forceinline__ int find_cell(const int *tpre, int f)
+{
+    int lo = 0, hi = kNbr;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const int mid = (lo + hi) >> 1;
+        if (tpre[mid] <= f) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Gather sources [base, base + B) of the flattened neighbourhood into buf
+// (cp.async); entries past `total` become far-away padding.  The table slot
+// of each gathered entry is kept in tc[] for the shift pass.
+template <int B, bool ADJ>
+__device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float4 *wbuf, const int *tstart,
+                                            const int *tpre, int base, int total, int lane, int (&tc)[B / 32])
+{
+#pragma unroll
+    for (int m = 0; m < B / 32; ++m) {
+        const int f = base + m * 32 + lane;
+        const int slot = m * 32 + lane;
+        if (f < total) {
+            const int t = find_cell(tpre, f);
+            const int src = tstart[t] + (f - tpre[t]);
+            cp_async16(buf + slot, bx.pos + src);
+            if (ADJ) cp_async16(wbuf + slot, bx.cot + src);
+            tc[m] = t;
+        } else {
+            buf[slot] = make_float4(kFar, kFar, kFar, 0.f);
+            if (ADJ) wbuf[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+            tc[m] = -1;
+        }
+    }
+    cp_async_commit();
+}
+
+// add the integer cell offset of each of this lane's landed entries
+template <int B>
+__device__ __forceinline__ void stage_shift(float4 *buf, int lane, const int (&tc)[B / 32])
+{
+#pragma unroll
+    for (int m = 0; m < B / 32; ++m) {
+        const int t = tc[m];
+        if (t >= 0) {
+            float4 v = buf[m * 32 + lane];
+            v.x += static_cast<float>(t / 25 - 2);
+            v.y += static_cast<float>((t / 5) % 5 - 2);
+            v.z += static_cast<float>(t % 5 - 2);
+            buf[m * 32 + lane] = v;
+        }
+    }
+}
+
+// S = 0: split mode (<= 16 sinks); S = 1, 2, 4: sinks per lane
+template <int S, int B, bool COMP, bool ADJ>
+__device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, float4 *wstage, int *tstart, int *tpre,
+                         int lane)
+{
+    constexpr bool SPLIT = (S == 0);
+    constexpr int SS = SPLIT ? 1 : S;
+    const int count = item.sink_count;
+    int logp = 0;
+    if (SPLIT) {
+        while ((1 << logp) < count) ++logp;
+    }
+    const int P = 1 << logp;
+    const int my_split = SPLIT ? (lane >> logp) : 0;
+    const int splits = SPLIT ? (32 >> logp) : 1;
+
+    float xi[SS], yi[SS], zi[SS], wx[SS], wy[SS], wz[SS];
+    float px[SS], py[SS], pz[SS];
+    Comp3 acc[SS];
+#pragma unroll
+    for (int s = 0; s < SS; ++s) {
+        const int k = SPLIT ? (lane & (P - 1)) : lane + 32 * s;
+        const int idx = item.sink_begin + min(k, count - 1);
+        const float4 p = __ldg(bx.pos + idx);
+        xi[s] = p.x; yi[s] = p.y; zi[s] = p.z;
+        if (ADJ) {
+            const float4 w = __ldg(bx.cot + idx);
+            wx[s] = w.x; wy[s] = w.y; wz[s] = w.z;
+        } else {
+            wx[s] = wy[s] = wz[s] = 0.f;
+        }
+        px[s] = py[s] = pz[s] = 0.f;
+        comp_init(acc[s]);
+    }
+    const float a0 = bx.a0, a1 = bx.a1, a2 = bx.a2, eps2 = bx.eps2;
+
+    const int total = build_table(bx, item.cell, tstart, tpre, lane);
+    const int rounds = (total + B - 1) / B;
+
+    int tc_cur[B / 32], tc_next[B / 32];
+#pragma unroll
+    for (int m = 0; m < B / 32; ++m) tc_next[m] = -1;
+    if (rounds > 0) stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, 0, total, lane, tc_cur);
+    for (int r = 0; r < rounds; ++r) {
+        float4 *buf = stage + (r & 1) * B;
+        float4 *wbuf = wstage + (r & 1) * B;
+        if (r + 1 < rounds) {
+            stage_issue<B, ADJ>(bx, stage + ((r + 1) & 1) * B, wstage + ((r + 1) & 1) * B, tstart, tpre, (r + 1) * B,
+                                total, lane, tc_next);
+            cp_async_wait_1();
+        } else {
+            cp_async_wait_0();
+        }
+        stage_shift<B>(buf, lane, tc_cur);
+        __syncwarp();
+        const int nr = min(B, total - r * B);
+        if (SPLIT) {
+            for (int j = my_split; j < nr; j += splits) {
+                if (ADJ)
+                    pair_adjoint(buf[j], wbuf[j], xi[0], yi[0], zi[0], wx[0], wy[0], wz[0], px[0], py[0], pz[0], a0,
+                                 a1, a2, eps2);
+                else
+                    pair_force(buf[j], xi[0], yi[0], zi[0], px[0], py[0], pz[0], a0, a1, a2);
+            }
+        } else {
+            const int nr4 = (nr + 3) & ~3;   // padding entries add exact zeros
+            for (int j = 0; j < nr4; j += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float4 q = buf[j + u];
+                    if (ADJ) {
+                        const float4 wq = wbuf[j + u];
+#pragma unroll
+                        for (int s = 0; s < SS; ++s)
+                            pair_adjoint(q, wq, xi[s], yi[s], zi[s], wx[s], wy[s], wz[s], px[s], py[s], pz[s], a0, a1,
+                                         a2, eps2);
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < SS; ++s)
+                            pair_force(q, xi[s], yi[s], zi[s], px[s], py[s], pz[s], a0, a1, a2);
+                    }
+                }
+            }
+        }
+        if (COMP) {
+#pragma unroll
+            for (int s = 0; s < SS; ++s) comp_fold(acc[s], px[s], py[s], pz[s]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < B / 32; ++m) tc_cur[m] = tc_next[m];
+    }
+    if (!COMP) {
+#pragma unroll
+        for (int s = 0; s < SS; ++s) {
+            acc[s].hx = px[s]; acc[s].hy = py[s]; acc[s].hz = pz[s];
+        }
+    }
+    if (SPLIT) {
+        for (int o = P; o < 32; o <<= 1) {
+            if (COMP) {
+                comp_xor_combine(acc[0], o);
+            } else {
+                acc[0].hx += __shfl_xor_sync(kFull, acc[0].hx, o);
+                acc[0].hy += __shfl_xor_sync(kFull, acc[0].hy, o);
+                acc[0].hz += __shfl_xor_sync(kFull, acc[0].hz, o);
+            }
+        }
+    }
+    const double scale = ADJ ? bx.grad_scale : bx.acc_scale;
+#pragma unroll
+    for (int s = 0; s < SS; ++s) {
+        const int k = SPLIT ? lane : lane + 32 * s;
+        if (k < count) {
+            const int idx = item.sink_begin + k;
+            const double gx = (static_cast<double>(acc[s].hx) + static_cast<double>(acc[s].lx)) * scale;
+            const double gy = (static_cast<double>(acc[s].hy) + static_cast<double>(acc[s].ly)) * scale;
+            const double gz = (static_cast<double>(acc[s].hz) + static_cast<double>(acc[s].lz)) * scale;
+            if (bx.acc64) {
+                double *o = bx.acc64 + 3 * static_cast<int64_t>(idx);
+                o[0] = gx; o[1] = gy; o[2] = gz;
+            }
+            if (bx.acc_out)
+                bx.acc_out[idx] =
+                    make_float4(static_cast<float>(gx), static_cast<float>(gy), static_cast<float>(gz), 0.f);
+        }
+    }
+}
+
+template <int B, bool COMP, bool ADJ>
+__global__ void __launch_bounds__(256) pair_kernel(const BoxDev *__restrict__ boxes, const Item *__restrict__ items,
+                                                   const int *__restrict__ n_items_p, int *__restrict__ queue)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    constexpr int PER_WARP_F4 = (ADJ ? 4 : 2) * B;
+    float4 *stage = reinterpret_cast<float4 *>(smem_raw) + warp * PER_WARP_F4;
+    float4 *wstage = stage + 2 * B;
+    int *tabs = reinterpret_cast<int *>(reinterpret_cast<float4 *>(smem_raw) + nwarps * PER_WARP_F4) + warp * 256;
+    int *tstart = tabs, *tpre = tabs + 128;
+    const int n_items = *n_items_p;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(queue, 1);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_items) break;
+        const Item item = items[it];
+        const BoxDev &bx = boxes[item.box];
+        if (item.sink_count <= 16)
+            run_item<0, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, lane);
+        else if (item.sink_count <= 32)
+            run_item<1, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, lane);
+        else if (item.sink_count <= 64)
+            run_item<2, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, lane);
+        else
+            run_item<4, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, lane);
+        __syncwarp();
+    }
+}
+
+template <int B, bool COMP, bool ADJ>
+size_t smem_bytes(int warps)
+{
+    return static_cast<size_t>(warps) * ((ADJ ? 4 : 2) * B * sizeof(float4) + 256 * sizeof(int));
+}
+
+template <int B, bool COMP, bool ADJ>
+cudaError_t launch_t(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, PairShape shape,
+                     int sm_count, cudaStream_t st)
+{
+    auto kern = pair_kernel<B, COMP, ADJ>;
+    const size_t smem = smem_bytes<B, COMP, ADJ>(shape.warps);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    int blocks = shape.blocks;
+    if (blocks <= 0) {
+        int per_sm = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, shape.warps * 32, smem);
+        if (err != cudaSuccess) return err;
+        blocks = sm_count * (per_sm > 0 ? per_sm : 1);
+    }
+    kern<<<blocks, shape.warps * 32, smem, st>>>(boxes, items, n_items, queue);
+    return cudaGetLastError();
+}
+
+template <int B, bool COMP, bool ADJ>
+int max_blocks_t(PairShape shape)
+{
+    int per_sm = 0;
+    auto kern = pair_kernel<B, COMP, ADJ>;
+    const size_t smem = smem_bytes<B, COMP, ADJ>(shape.warps);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, shape.warps * 32, smem) != cudaSuccess) return 0;
+    return per_sm;
+}
+
+}  // namespace
+
+#define NF_PAIR_DISPATCH(FN, ...)                                                                                   \
+    do {                                                                                                            \
+        if (shape.stage == 256) {                                                                                   \
+            if (adjoint) return compensated ? FN<256, true, true>(__VA_ARGS__) : FN<256, false, true>(__VA_ARGS__); \
+            return compensated ? FN<256, true, false>(__VA_ARGS__) : FN<256, false, false>(__VA_ARGS__);            \
+        }                                                                                                           \
+        if (adjoint) return compensated ? FN<128, true, true>(__VA_ARGS__) : FN<128, false, true>(__VA_ARGS__);     \
+        return compensated ? FN<128, true, false>(__VA_ARGS__) : FN<128, false, false>(__VA_ARGS__);                \
+    } while (0)
+
+cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, int compensated,
+                        int adjoint, PairShape shape, int sm_count, cudaStream_t st)
+{
+    if (shape.warps < 1 || shape.warps > 8 || (shape.stage != 128 && shape.stage != 256)) return cudaErrorInvalidValue;
+    NF_PAIR_DISPATCH(launch_t, boxes, items, n_items, queue, shape, sm_count, st);
+}
+
+int pair_max_blocks_per_sm(int compensated, int adjoint, PairShape shape)
+{
+    if (shape.warps < 1 || shape.warps > 8 || (shape.stage != 128 && shape.stage != 256)) return 0;
+    NF_PAIR_DISPATCH(max_blocks_t, shape);
+}
+
+}  // namespace nf
