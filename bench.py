@@ -1,0 +1,339 @@
+"""Benchmark of the near-field step on the clustered 512^3 workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step is one pass of the whole hot path over the box: the pair kernel
+(nf_forces: work queue, source staging, pair sum, compensated accumulation)
+then the FP64 kick-drift with re-binning (nf_kick_drift: kick, drift, stable
+radix sort by cell, cell table, work-queue plan).  The metric is near-field
+pair interactions per second (one ordered sink-source evaluation per pair,
+self pairs included); particles per second per step is reported beside it.
+Inputs are resident in HBM when the timed region starts and are larger than
+L2 (2.1 GB of positions).  The plain FP32 kernel is timed on the same
+positions for comparison, and both are checked against the FP64 oracle on
+sampled sinks.
+
+`--impl reference` times the FP64 CPU oracle (the reference of this build) on
+the same workload: each step evaluates a bounded sample of sinks.
+
+Under torchrun (N > 1) every rank runs its own replica of the workload on its
+own GPU (weak scaling; the near-field of one box needs no exchange here);
+only the timing is reduced across ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "zeldovich512"
+METRIC = "near-field Gpair-interactions/s and particles/s/step at 512^3 clustered vs plain FP32 kernel"
+UNIT = "Gpair/s"
+OPS_PER_PAIR = 20          # FP32-pipe operations of the pair arithmetic (issue roofline)
+FP32_LANES_PER_SM = 128
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=mx, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"sm_max_mhz": 2032.0}, "fallback"
+
+
+def _make_workload(name):
+    from synth import workload
+    return workload(name)
+
+
+def _oracle_sample(w, b, k, seed):
+    """Oracle FP64 forces on k sampled sinks: (acc, sumabs, pairs, seconds, sinks)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    sinks = np.sort(rng.choice(b.n, k, replace=False)).astype(np.int64)
+    t = time.perf_counter()
+    acc, sa, pairs = oracle.forces(b, w.eps, sinks, with_sumabs=True)
+    return acc, sa, pairs, time.perf_counter() - t, sinks
+
+
+def _sized_sample(w, b, target_s, seed):
+    """A sink count whose oracle pass takes about target_s seconds on this host."""
+    k = min(b.n, 20000)
+    _, _, _, t, _ = _oracle_sample(w, b, k, seed)
+    if t < 0.5 * target_s:
+        k = int(min(b.n, k * target_s / max(t, 1e-3)))
+    return k
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm (bounded sample of sinks per step)."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    w = _make_workload(WORKLOAD)
+    b = oracle.bin_positions(w.pos, w.cpd, w.box)
+    k = args.ref_sinks or _sized_sample(w, b, args.ref_seconds, seed=99)
+    times, pairs = [], []
+    for s in range(args.warmup + args.steps):
+        _, _, p, dt, _ = _oracle_sample(w, b, k, seed=100 + s)
+        if s >= args.warmup:
+            times.append(dt)
+            pairs.append(p)
+    value = sum(pairs) / sum(times) / 1e9
+    cores = os.cpu_count()
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * sum(times) / len(times), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic (seeded Zel'dovich lattice + Plummer halos)", impl="reference",
+                config=dict(workload=f"{WORKLOAD}: N=512^3, CPD=405, R=2, eps=1/50 spacing", sinks_per_step=k),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle",
+                                  sample=f"{k} uniformly sampled sinks per step, all their near-field pairs"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _launches_per_step(cpd):
+    """Kernels the library launches per step: forces (1) + kick-drift.
+
+    kick-drift: kick 1, drift 1, count 1, radix sort (hist, 3 scan kernels,
+    scatter per 8-bit pass), gather 1, cell-start scan 3, plan (1 reset +
+    5 classes x (counts, 3 scan kernels, emit, advance)).
+    """
+    ncell = cpd ** 3
+    bits = max(1, (ncell - 1).bit_length())
+    passes = (bits + 7) // 8
+    kick_drift = 1 + 1 + 1 + 5 * passes + 1 + 3 + (1 + 5 * 6)
+    return 1 + kick_drift
+
+
+def run(args):
+    import torch
+    import paper_1810_02916_b300 as nfb
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    stream = torch.cuda.Stream()
+
+    w = _make_workload(WORKLOAD)
+    nf = nfb.NearField(w.cpd, w.eps, w.box)
+    nf.set_stream(stream)
+    Xd = torch.from_numpy(w.pos).to(f"cuda:{dev}")
+    nf.bin_particles(Xd)
+    del Xd
+    n = nf.n
+    pairs = nf.pair_count()
+    acc_d = torch.empty((n, 4), dtype=torch.float32, device=f"cuda:{dev}")
+
+    # time step: max|a| dt^2 <= 0.1 eps (so max |v| dt stays far below 0.8 cells)
+    with torch.cuda.stream(stream):
+        nf.forces(acc_d)
+    torch.cuda.synchronize()
+    amax = float(acc_d[:, :3].abs().max())
+    dt = (0.1 * w.eps / amax) ** 0.5
+
+    def step():
+        nf.forces(False)
+        nf.kick_drift(dt)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(dev)
+    clocks.start()
+    nf.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    nf.profile(False)
+    step_ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    launches, pair_ms = nf.profile_read()
+    pair_ms /= max(launches, 1)
+    t_max = step_ms
+    if world > 1:
+        t = torch.tensor([step_ms], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * pairs / (t_max * 1e-3) / 1e9
+    pair_kernel_gps = pairs / (pair_ms * 1e-3) / 1e9
+
+    # plain FP32 kernel on the same positions, and accuracy of both on sampled sinks
+    import oracle
+    extra = {}
+    if rank == 0:
+        b = oracle.bin_positions(w.pos, w.cpd, w.box)   # layout of the current state differs after steps:
+        nf_cmp = nfb.NearField(w.cpd, w.eps, w.box)      # compare on a fresh box of the initial positions
+        nf_cmp.set_stream(stream)
+        nf_cmp.bin_particles(torch.from_numpy(w.pos).to(f"cuda:{dev}"))
+        acc_c = nf_cmp.forces()
+        nf_cmp.set_accumulation(nfb.ACC_PLAIN)
+        nf_cmp.profile(True)
+        for _ in range(3):
+            nf_cmp.forces(acc_d)
+        k, ms = nf_cmp.profile_read()
+        acc_p = nf_cmp.forces()
+        nf_cmp.close()
+        ref, sa, _, _, sinks = _oracle_sample(w, b, 20000, seed=7)
+        ec = oracle.error_stats(acc_c[sinks, :3], ref, sa)
+        ep = oracle.error_stats(acc_p[sinks, :3], ref, sa)
+        kc = args.cpu_sinks or _sized_sample(w, b, args.cpu_seconds, seed=8)
+        _, _, sampled_pairs, cpu_s, _ = _oracle_sample(w, b, kc, seed=9)
+        extra = dict(
+            compensated=dict(pair_kernel_gpair_s=pair_kernel_gps, error_vs_oracle=ec),
+            plain_fp32=dict(pair_kernel_gpair_s=pairs / (ms / k * 1e-3) / 1e9, error_vs_oracle=ep),
+            cpu_baseline=dict(value=sampled_pairs / cpu_s / 1e9, unit=UNIT, cores=os.cpu_count(), kind="oracle",
+                              sample=f"{kc} uniformly sampled sinks of the workload "
+                                     f"({sampled_pairs} pairs, {cpu_s:.1f} s)"),
+        )
+
+    # end to end through the C ABI with pinned host buffers: positions in, accelerations out
+    e2e = None
+    if rank == 0 and args.e2e_steps > 0:
+        xh = torch.from_numpy(w.pos).pin_memory()
+        ah = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+        nf_e = nfb.NearField(w.cpd, w.eps, w.box)
+        nf_e.set_stream(stream)
+
+        def e2e_step():
+            nf_e.bin_particles(xh)
+            nf_e.forces(ah)
+            nf_e.kick_drift(dt)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_s = (time.perf_counter() - t0) / args.e2e_steps
+        nf_e.close()
+        e2e = dict(value=pairs / e_s / 1e9, unit=UNIT, h2d_bytes_per_step=int(xh.numel() * 8),
+                   d2h_bytes_per_step=int(ah.numel() * 4),
+                   step="nf_bin_particles(pinned host xyz) + nf_forces(pinned host acc) + nf_kick_drift")
+
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_gps = props.multi_processor_count * sm_max * 1e6 * FP32_LANES_PER_SM / OPS_PER_PAIR / 1e9
+    if rank == 0:
+        line = dict(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=t_max, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+            data="synthetic (seeded Zel'dovich lattice + Plummer halos)",
+            config=dict(workload=f"{WORKLOAD}: N=512^3=134217728, CPD=405, R=2, eps=1/50 spacing, "
+                                 "Zel'dovich P(k)~k^-1.5 + 2000 Plummer halos",
+                        pairs_per_step=pairs, particles=n, dt=dt,
+                        parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                        l2="inputs larger than L2 (2.1 GB positions, 3.2 GB FP64 sums)"),
+            particles_per_s_per_step=world * n / (t_max * 1e-3),
+            gpu_launches=_launches_per_step(w.cpd) * args.steps,
+            roofline=dict(bound="alu", achieved=pair_kernel_gps, peak=peak_gps, unit=UNIT,
+                          frac=pair_kernel_gps / peak_gps, traffic=None,
+                          peak_basis=f"FP32 issue roofline: {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
+                                     f"({src}) x 128 lanes / {OPS_PER_PAIR} ops per pair"),
+            clocks=clk, e2e=e2e, **extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sinks", type=int, default=0, help="0: size the sample to --cpu-seconds")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-sinks", type=int, default=0, help="0: size the sample to --ref-seconds")
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -39,6 +39,10 @@
 extern "C" {
 #endif
 
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 typedef struct nf_box nf_t;
 
 enum nf_status {
@@ -206,6 +210,10 @@ int nf_profile_read(nf_t *nf, int64_t *launches, double *ms);
  */
 int nf_set_shape(nf_t *nf, int warps, int stage);
 int nf_tune(nf_t *nf, char *report, int report_len);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,271 @@
+"""B300 near-field direct sum of the Abacus N-body method (arXiv:1810.02916).
+
+Thin ctypes binding over the C ABI in include/nearfield.h (libnearfield.so,
+built in-tree by `paper_1810_02916_b300.build`).  This module only marshals
+arguments: every step of the computation runs in the library's CUDA
+kernels.  If the library is missing the import of any entry point fails with
+an error; there is no CPU fallback.
+
+Arrays may be NumPy arrays (host) or CUDA torch tensors (device); both are
+passed to the library as plain pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnearfield.so")
+
+NF_OK, NF_EINVAL, NF_ENOMEM, NF_ECUDA, NF_ETIMEOUT, NF_ESTATE = range(6)
+ACC_COMPENSATED, ACC_PLAIN = 0, 1
+_STATUS = {1: "NF_EINVAL", 2: "NF_ENOMEM", 3: "NF_ECUDA", 4: "NF_ETIMEOUT", 5: "NF_ESTATE"}
+
+EXPORTS = [
+    "nf_create", "nf_destroy", "nf_last_error", "nf_set_stream", "nf_set_accumulation", "nf_bin_particles",
+    "nf_set_particles", "nf_set_velocities", "nf_get_particles", "nf_num_particles", "nf_pair_count", "nf_forces",
+    "nf_get_forces64", "nf_kick_drift", "nf_vjp", "nf_forces_batched", "nf_profile", "nf_profile_read",
+    "nf_set_shape", "nf_tune",
+]
+
+
+class NearFieldError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnearfield.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_1810_02916_b300.build` "
+                               "(the CUDA library is required; there is no fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        p, i, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "nf_create": ([i, i, d, d, ctypes.POINTER(p)], i),
+            "nf_destroy": ([p], None),
+            "nf_last_error": ([p], ctypes.c_char_p),
+            "nf_set_stream": ([p, p], i),
+            "nf_set_accumulation": ([p, i], i),
+            "nf_bin_particles": ([p, p, i64], i),
+            "nf_set_particles": ([p, p, p, p, i64], i),
+            "nf_set_velocities": ([p, p], i),
+            "nf_get_particles": ([p, p, p, p, p, p], i),
+            "nf_num_particles": ([p, ctypes.POINTER(i64)], i),
+            "nf_pair_count": ([p, ctypes.POINTER(i64)], i),
+            "nf_forces": ([p, p], i),
+            "nf_get_forces64": ([p, p], i),
+            "nf_kick_drift": ([p, d], i),
+            "nf_vjp": ([p, p, p], i),
+            "nf_forces_batched": ([ctypes.POINTER(p), i, ctypes.POINTER(p)], i),
+            "nf_profile": ([p, i], i),
+            "nf_profile_read": ([p, ctypes.POINTER(i64), ctypes.POINTER(d)], i),
+            "nf_set_shape": ([p, i, i], i),
+            "nf_tune": ([p, ctypes.c_char_p, i], i),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    """Data pointer of a NumPy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check_arr(a, dtype, shape, name):
+    if a is None:
+        return
+    dt = str(a.dtype).replace("torch.", "")
+    if dt != np.dtype(dtype).name:
+        raise TypeError(f"{name}: dtype {dt}, expected {np.dtype(dtype).name}")
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(a.shape)}, expected {tuple(shape)}")
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class NearField:
+    """One periodic box: cpd^3 cells, near-field radius R = 2, spline softening eps (box units)."""
+
+    def __init__(self, cpd: int, eps: float, box: float = 1.0, R: int = 2):
+        h = ctypes.c_void_p()
+        rc = lib().nf_create(int(cpd), int(R), float(eps), float(box), ctypes.byref(h))
+        if rc != NF_OK:
+            raise NearFieldError(rc, lib().nf_last_error(None).decode())
+        self._h = h
+        self.cpd, self.eps, self.box, self.R = int(cpd), float(eps), float(box), int(R)
+
+    # -------------------------------------------------------------- plumbing
+    @property
+    def handle(self):
+        return self._h
+
+    def _call(self, name, *args):
+        rc = getattr(lib(), name)(self._h, *args)
+        if rc != NF_OK:
+            raise NearFieldError(rc, lib().nf_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n(self) -> int:
+        v = ctypes.c_int64()
+        self._call("nf_num_particles", ctypes.byref(v))
+        return int(v.value)
+
+    @property
+    def ncell(self) -> int:
+        return self.cpd ** 3
+
+    def set_stream(self, stream):
+        self._call("nf_set_stream", _stream_handle(stream))
+
+    def set_accumulation(self, mode: int):
+        self._call("nf_set_accumulation", int(mode))
+
+    # -------------------------------------------------------------- particles
+    def bin_particles(self, xyz):
+        """Load global positions (n, 3) float64 in box units (NumPy or CUDA tensor)."""
+        n = int(xyz.shape[0])
+        _check_arr(xyz, np.float64, (n, 3), "xyz")
+        self._call("nf_bin_particles", _ptr(xyz), n)
+
+    def set_particles(self, cell_offsets, counts, pos):
+        n = int(pos.shape[0])
+        _check_arr(cell_offsets, np.int64, (self.ncell + 1,), "cell_offsets")
+        _check_arr(counts, np.int32, (self.ncell,), "counts")
+        _check_arr(pos, np.float32, (n, 4), "pos")
+        self._call("nf_set_particles", _ptr(cell_offsets), _ptr(counts), _ptr(pos), n)
+
+    def set_velocities(self, vel):
+        _check_arr(vel, np.float32, (self.n, 4), "vel")
+        self._call("nf_set_velocities", _ptr(vel))
+
+    def get_particles(self):
+        """State in storage order: offsets, counts, pos (n,4), vel (n,4), perm (n,) as NumPy arrays."""
+        n = self.n
+        out = dict(cell_offsets=np.empty(self.ncell + 1, np.int64), counts=np.empty(self.ncell, np.int32),
+                   pos=np.empty((n, 4), np.float32), vel=np.empty((n, 4), np.float32), perm=np.empty(n, np.int64))
+        self._call("nf_get_particles", _ptr(out["cell_offsets"]), _ptr(out["counts"]), _ptr(out["pos"]),
+                   _ptr(out["vel"]), _ptr(out["perm"]))
+        return out
+
+    def pair_count(self) -> int:
+        v = ctypes.c_int64()
+        self._call("nf_pair_count", ctypes.byref(v))
+        return int(v.value)
+
+    # -------------------------------------------------------------- compute
+    def forces(self, out=None):
+        """Accelerations (n, 4) float32, box units, storage order.
+
+        `out` may be a NumPy array or a CUDA tensor; None returns a new NumPy array.
+        Pass out=False to keep the result in the box only (FP64 sums for kick-drift).
+        """
+        if out is False:
+            self._call("nf_forces", None)
+            return None
+        if out is None:
+            out = np.empty((self.n, 4), np.float32)
+        _check_arr(out, np.float32, (self.n, 4), "out")
+        self._call("nf_forces", _ptr(out))
+        return out
+
+    def forces64(self, out=None):
+        if out is None:
+            out = np.empty((self.n, 3), np.float64)
+        _check_arr(out, np.float64, (self.n, 3), "out")
+        self._call("nf_get_forces64", _ptr(out))
+        if isinstance(out, np.ndarray):
+            self.synchronize()
+        return out
+
+    def kick_drift(self, dt: float):
+        self._call("nf_kick_drift", float(dt))
+
+    def vjp(self, w, out=None):
+        """d(sum_i w_i . a_i)/dx_k in box units, (n, 4) float32; w is (n, 4) float32."""
+        _check_arr(w, np.float32, (self.n, 4), "w")
+        if out is None:
+            out = np.empty((self.n, 4), np.float32)
+        _check_arr(out, np.float32, (self.n, 4), "out")
+        self._call("nf_vjp", _ptr(w), _ptr(out))
+        return out
+
+    def synchronize(self):
+        v = ctypes.c_int64()
+        self._call("nf_num_particles", ctypes.byref(v))
+        try:
+            import torch
+            if torch.cuda.is_available():
+                torch.cuda.synchronize()
+        except ImportError:
+            pass
+
+    # -------------------------------------------------------------- tuning / timing
+    def profile(self, enable: bool = True):
+        self._call("nf_profile", 1 if enable else 0)
+
+    def profile_read(self):
+        """(launches, total ms) of the pair kernel since the last read."""
+        k, ms = ctypes.c_int64(), ctypes.c_double()
+        self._call("nf_profile_read", ctypes.byref(k), ctypes.byref(ms))
+        return int(k.value), float(ms.value)
+
+    def set_shape(self, warps: int, stage: int):
+        self._call("nf_set_shape", int(warps), int(stage))
+
+    def tune(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        self._call("nf_tune", buf, 512)
+        return buf.value.decode()
+
+
+def forces_batched(boxes, outs=None):
+    """Forces of several boxes in one persistent launch; outs: list of arrays/tensors or None."""
+    nb = len(boxes)
+    harr = (ctypes.c_void_p * nb)(*[b.handle for b in boxes])
+    if outs is None:
+        outs = [np.empty((b.n, 4), np.float32) for b in boxes]
+    oarr = (ctypes.c_void_p * nb)(*[_ptr(o) for o in outs])
+    rc = lib().nf_forces_batched(harr, nb, oarr)
+    if rc != NF_OK:
+        raise NearFieldError(rc, lib().nf_last_error(boxes[0].handle).decode())
+    return outs

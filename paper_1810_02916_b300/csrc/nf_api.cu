@@ -1,0 +1,927 @@
+// nf_api.cu -- the C ABI of include/nearfield.h: box state, input
+// validation, data movement, and the order of device work for each call.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/nearfield.h"
+#include "nf_internal.cuh"
+
+using nf::BoxDev;
+using nf::Item;
+using nf::PairShape;
+
+namespace {
+
+thread_local std::string g_create_error;
+std::atomic<uint64_t> g_generation{0};   // process-wide, so a reused box address never matches a stale plan
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct nf_box {
+    // geometry (Section 2.1)
+    int cpd = 0, R = 2, ncell = 0;
+    double eps = 0, box = 0, w = 0, inv_w = 0;
+    int device = 0, sm_count = 0;
+    cudaStream_t stream = nullptr;
+    int acc_mode = NF_ACC_COMPENSATED;
+    PairShape shape{8, 128, 0};
+
+    int64_t n = 0, cap = 0, item_cap = 0;
+    bool have_particles = false, have_forces = false;
+    uint64_t generation = 0;
+
+    // particle state, storage order
+    float4 *pos = nullptr, *vel = nullptr;
+    double *acc64 = nullptr;
+    float4 *acc32 = nullptr;          // FP32 output staging for host outputs
+    float4 *cot = nullptr;            // cotangent staging
+    uint32_t *keys[2] = {nullptr, nullptr}, *vals[2] = {nullptr, nullptr};
+    int cur = 0;                      // keys[cur] = cell of each stored particle, vals[cur] = its id
+    // per-id scratch used by binning and re-binning
+    float4 *xq_by_id = nullptr, *vel_by_id = nullptr, *vel_tmp = nullptr;
+    // cells
+    int *cell_start = nullptr, *counts = nullptr, *offsets = nullptr;
+    void *scan_tmp = nullptr, *radix_tmp = nullptr;
+    size_t radix_tmp_bytes = 0;
+    // plan
+    Item *items = nullptr;
+    int *n_items = nullptr, *queue = nullptr, *err = nullptr;
+    unsigned long long *pairs = nullptr;
+    BoxDev *d_box = nullptr;
+    BoxDev h_box{};                   // host mirror of *d_box
+    bool box_dirty = true;
+    // staging for host inputs
+    DevBuf stage;
+    // pointer-kind cache (avoids attribute queries in repeated calls)
+    const void *last_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool last_dev[4] = {false, false, false, false};
+    // profiling
+    bool profile = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+
+    std::string last_error;
+};
+
+namespace {
+
+int fail(nf_t *nf, int code, const std::string &msg)
+{
+    if (nf) nf->last_error = msg;
+    return code;
+}
+
+int cuda_fail(nf_t *nf, const char *what, cudaError_t e)
+{
+    return fail(nf, NF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define NF_CK(call)                                                         \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return cuda_fail(nf, #call, e_);             \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// cached per call site (slot) so that repeated calls with the same pointer
+// make no attribute query
+bool is_device_cached(nf_t *nf, int slot, const void *p)
+{
+    if (p && p == nf->last_ptr[slot]) return nf->last_dev[slot];
+    const bool d = is_device_ptr(p);
+    nf->last_ptr[slot] = p;
+    nf->last_dev[slot] = d;
+    return d;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <class T>
+int dalloc(nf_t *nf, T **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(nf, NF_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
+                                       cudaGetErrorString(e));
+    }
+    return NF_OK;
+}
+
+template <class T>
+void dfree(T *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+int ensure_stage(nf_t *nf, size_t bytes)
+{
+    if (nf->stage.bytes >= bytes) return NF_OK;
+    if (nf->stage.p) cudaFree(nf->stage.p);
+    nf->stage.p = nullptr;
+    nf->stage.bytes = 0;
+    int rc = dalloc(nf, &nf->stage.p, bytes);
+    if (rc == NF_OK) nf->stage.bytes = bytes;
+    return rc;
+}
+
+// a device copy of a caller input: the pointer itself if it is device memory
+// (and 16-byte aligned), else the staging buffer after an async copy
+int device_input(nf_t *nf, int slot, const void *src, size_t bytes, const void **out)
+{
+    if (is_device_cached(nf, slot, src) && aligned16(src)) {
+        *out = src;
+        return NF_OK;
+    }
+    int rc = ensure_stage(nf, bytes);
+    if (rc != NF_OK) return rc;
+    NF_CK(cudaMemcpyAsync(nf->stage.p, src, bytes, cudaMemcpyDefault, nf->stream));
+    *out = nf->stage.p;
+    return NF_OK;
+}
+
+void free_particles(nf_t *nf)
+{
+    dfree(nf->pos); dfree(nf->vel); dfree(nf->acc64); dfree(nf->acc32); dfree(nf->cot);
+    for (int k = 0; k < 2; ++k) { dfree(nf->keys[k]); dfree(nf->vals[k]); }
+    dfree(nf->xq_by_id); dfree(nf->vel_by_id); dfree(nf->vel_tmp);
+    dfree(nf->items);
+    if (nf->radix_tmp) cudaFree(nf->radix_tmp);
+    nf->radix_tmp = nullptr;
+    nf->radix_tmp_bytes = 0;
+    nf->cap = 0;
+    nf->item_cap = 0;
+}
+
+int ensure_capacity(nf_t *nf, int64_t n)
+{
+    const int64_t item_cap = std::min<int64_t>(n, nf->ncell) + n / nf::kTile + 16;
+    if (n <= nf->cap && item_cap <= nf->item_cap && nf->pos) return NF_OK;
+    cudaStreamSynchronize(nf->stream);
+    free_particles(nf);
+    const int64_t c = n < 1 ? 1 : n;
+    int rc = NF_OK;
+    const size_t f4 = sizeof(float4) * static_cast<size_t>(c);
+    const size_t u4 = sizeof(uint32_t) * static_cast<size_t>(c);
+    if ((rc = dalloc(nf, &nf->pos, f4)) || (rc = dalloc(nf, &nf->vel, f4)) ||
+        (rc = dalloc(nf, &nf->acc64, 3 * sizeof(double) * static_cast<size_t>(c))) ||
+        (rc = dalloc(nf, &nf->keys[0], u4)) || (rc = dalloc(nf, &nf->keys[1], u4)) ||
+        (rc = dalloc(nf, &nf->vals[0], u4)) || (rc = dalloc(nf, &nf->vals[1], u4)) ||
+        (rc = dalloc(nf, &nf->xq_by_id, f4)) || (rc = dalloc(nf, &nf->vel_by_id, f4)) ||
+        (rc = dalloc(nf, &nf->vel_tmp, f4)) ||
+        (rc = dalloc(nf, &nf->items, sizeof(Item) * static_cast<size_t>(item_cap)))) {
+        free_particles(nf);
+        return rc;
+    }
+    nf->radix_tmp_bytes = nf::radix_temp_bytes(c);
+    if ((rc = dalloc(nf, &nf->radix_tmp, nf->radix_tmp_bytes))) {
+        free_particles(nf);
+        return rc;
+    }
+    nf->cap = c;
+    nf->item_cap = item_cap;
+    nf->box_dirty = true;
+    return NF_OK;
+}
+
+int key_bits(int ncell)
+{
+    int b = 1;
+    while (b < 32 && (1ll << b) < ncell) ++b;
+    return b;
+}
+
+void fill_box_desc(nf_t *nf, BoxDev &b, float4 *acc_out, double *acc64, const float4 *cot)
+{
+    const double ec = nf->eps * nf->inv_w;   // eps in cell units
+    b.pos = nf->pos;
+    b.cell_start = nf->cell_start;
+    b.acc_out = acc_out;
+    b.acc64 = acc64;
+    b.cot = cot;
+    b.cpd = nf->cpd;
+    b.n = static_cast<int>(nf->n);
+    b.a0 = static_cast<float>(10.0 / (ec * ec * ec));
+    b.a1 = static_cast<float>(-15.0 / (ec * ec * ec * ec));
+    b.a2 = static_cast<float>(6.0 / (ec * ec * ec * ec * ec));
+    b.eps2 = static_cast<float>(ec * ec);
+    b.acc_scale = nf->inv_w * nf->inv_w;
+    b.grad_scale = nf->inv_w * nf->inv_w * nf->inv_w;
+}
+
+int upload_box(nf_t *nf, float4 *acc_out, double *acc64, const float4 *cot)
+{
+    BoxDev b{};
+    fill_box_desc(nf, b, acc_out, acc64, cot);
+    if (nf->box_dirty || std::memcmp(&b, &nf->h_box, sizeof(BoxDev)) != 0) {
+        nf->h_box = b;
+        NF_CK(cudaMemcpyAsync(nf->d_box, &nf->h_box, sizeof(BoxDev), cudaMemcpyHostToDevice, nf->stream));
+        nf->box_dirty = false;
+    }
+    return NF_OK;
+}
+
+// items of this box (all classes, largest first) into nf->items
+int plan(nf_t *nf)
+{
+    NF_CK(nf::zero_device_int(nf->n_items, nf->stream));
+    for (int cls = 0; cls < nf::kClasses; ++cls)
+        NF_CK(nf::plan_items_class(nf->cell_start, nf->ncell, 0, cls, nf->items, nf->n_items, nf->counts,
+                                   nf->offsets, nf->scan_tmp, nf->stream));
+    return NF_OK;
+}
+
+// counts[0..ncell] -> cell_start (exclusive scan), counts[ncell] must be 0
+int counts_to_cell_start(nf_t *nf)
+{
+    NF_CK(nf::exclusive_scan_i32(nf->counts, nf->cell_start, static_cast<int64_t>(nf->ncell) + 1, nf->scan_tmp,
+                                 nf->stream));
+    return NF_OK;
+}
+
+// sort (keys[src], vals[src]) by key; gather positions (and velocities)
+int sort_and_gather(nf_t *nf, int src, bool with_vel)
+{
+    int in_alt = 0;
+    NF_CK(nf::radix_sort_pairs(nf->keys[src], nf->vals[src], nf->keys[1 - src], nf->vals[1 - src], nf->n,
+                               key_bits(nf->ncell), nf->radix_tmp, &in_alt, nf->stream));
+    nf->cur = in_alt ? 1 - src : src;
+    NF_CK(nf::gather_sorted(nf->vals[nf->cur], nf->xq_by_id, with_vel ? nf->vel_by_id : nullptr, nf->pos, nf->vel,
+                            static_cast<int>(nf->n), nf->stream));
+    return NF_OK;
+}
+
+int read_err(nf_t *nf, int *host)
+{
+    NF_CK(cudaMemcpyAsync(host, nf->err, sizeof(int), cudaMemcpyDeviceToHost, nf->stream));
+    NF_CK(cudaStreamSynchronize(nf->stream));
+    return NF_OK;
+}
+
+int launch_forces(nf_t *nf, const BoxDev *d_boxes, const Item *items, const int *n_items, int *queue, int adjoint)
+{
+    NF_CK(cudaMemsetAsync(queue, 0, sizeof(int), nf->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (nf->profile) {
+        while (nf->ev.size() < nf->ev_used + 2) {
+            cudaEvent_t e;
+            NF_CK(cudaEventCreate(&e));
+            nf->ev.push_back(e);
+        }
+        e0 = nf->ev[nf->ev_used];
+        e1 = nf->ev[nf->ev_used + 1];
+        nf->ev_used += 2;
+        NF_CK(cudaEventRecord(e0, nf->stream));
+    }
+    NF_CK(nf::launch_pair(d_boxes, items, n_items, queue, nf->acc_mode == NF_ACC_COMPENSATED, adjoint, nf->shape,
+                          nf->sm_count, nf->stream));
+    if (nf->profile) NF_CK(cudaEventRecord(e1, nf->stream));
+    return NF_OK;
+}
+
+int check_box(nf_t *nf)
+{
+    if (!nf) return NF_EINVAL;
+    cudaError_t e = cudaSetDevice(nf->device);
+    if (e != cudaSuccess) return cuda_fail(nf, "cudaSetDevice", e);
+    return NF_OK;
+}
+
+// widen / reformat state for nf_get_particles
+__global__ void k_offsets64(const int *cs, int ncell, int64_t *out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c <= ncell) out[c] = cs[c];
+}
+__global__ void k_counts32(const int *cs, int ncell, int32_t *out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) out[c] = cs[c + 1] - cs[c];
+}
+__global__ void k_perm64(const uint32_t *v, int n, int64_t *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = v[k];
+}
+
+inline int nblk(int64_t n) { return static_cast<int>((n + 255) / 256); }
+
+// write `bytes` produced by `produce(dst_device)` into a caller pointer
+template <class F>
+int produce_out(nf_t *nf, void *dst, size_t bytes, F produce)
+{
+    if (is_device_ptr(dst) && aligned16(dst)) return produce(dst);
+    int rc = ensure_stage(nf, bytes);
+    if (rc != NF_OK) return rc;
+    rc = produce(nf->stage.p);
+    if (rc != NF_OK) return rc;
+    NF_CK(cudaMemcpyAsync(dst, nf->stage.p, bytes, cudaMemcpyDefault, nf->stream));
+    return NF_OK;
+}
+
+std::mutex g_tune_mu;
+std::map<std::string, PairShape> g_tune_cache;
+
+}  // namespace
+
+extern "C" {
+
+int nf_create(int cpd, int R, double eps, double box, nf_t **out)
+{
+    if (!out) return NF_EINVAL;
+    *out = nullptr;
+    g_create_error.clear();
+    if (R != 2) {
+        g_create_error = "only R = 2 is supported";
+        return NF_EINVAL;
+    }
+    if (cpd < 2 * R + 1 || static_cast<int64_t>(cpd) * cpd * cpd >= (1ll << 31) - 1) {
+        g_create_error = "cpd must satisfy 2R+1 <= cpd and cpd^3 < 2^31";
+        return NF_EINVAL;
+    }
+    if (!(box > 0) || !std::isfinite(box)) {
+        g_create_error = "box must be positive and finite";
+        return NF_EINVAL;
+    }
+    if (!(eps > 0) || !(eps < box / cpd)) {
+        g_create_error = "eps must satisfy 0 < eps < box / cpd";
+        return NF_EINVAL;
+    }
+    nf_t *nf = new (std::nothrow) nf_box();
+    if (!nf) {
+        g_create_error = "host allocation failed";
+        return NF_ENOMEM;
+    }
+    nf->cpd = cpd;
+    nf->R = R;
+    nf->ncell = cpd * cpd * cpd;
+    nf->eps = eps;
+    nf->box = box;
+    nf->w = box / cpd;
+    nf->inv_w = static_cast<double>(cpd) / box;
+    int rc = NF_OK;
+    cudaError_t e = cudaGetDevice(&nf->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nf->sm_count, cudaDevAttrMultiProcessorCount, nf->device);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        delete nf;
+        return NF_ECUDA;
+    }
+    const size_t cells = sizeof(int) * (static_cast<size_t>(nf->ncell) + 2);
+    if ((rc = dalloc(nf, &nf->cell_start, cells)) || (rc = dalloc(nf, &nf->counts, cells)) ||
+        (rc = dalloc(nf, &nf->offsets, cells)) ||
+        (rc = dalloc(nf, &nf->scan_tmp, nf::scan_temp_bytes(static_cast<int64_t>(nf->ncell) + 2))) ||
+        (rc = dalloc(nf, &nf->n_items, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->queue, sizeof(int) * 4)) ||
+        (rc = dalloc(nf, &nf->err, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->pairs, sizeof(unsigned long long))) ||
+        (rc = dalloc(nf, &nf->d_box, sizeof(BoxDev)))) {
+        g_create_error = nf->last_error;
+        nf_destroy(nf);
+        return rc;
+    }
+    e = cudaMemset(nf->cell_start, 0, cells);
+    if (e == cudaSuccess) e = cudaMemset(nf->n_items, 0, sizeof(int) * 4);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("cudaMemset: ") + cudaGetErrorString(e);
+        nf_destroy(nf);
+        return NF_ECUDA;
+    }
+    *out = nf;
+    return NF_OK;
+}
+
+void batch_forget(nf_t *nf);
+
+void nf_destroy(nf_t *nf)
+{
+    if (!nf) return;
+    batch_forget(nf);
+    cudaSetDevice(nf->device);
+    cudaStreamSynchronize(nf->stream);
+    free_particles(nf);
+    dfree(nf->cell_start); dfree(nf->counts); dfree(nf->offsets);
+    if (nf->scan_tmp) cudaFree(nf->scan_tmp);
+    dfree(nf->n_items); dfree(nf->queue); dfree(nf->err); dfree(nf->pairs); dfree(nf->d_box);
+    if (nf->stage.p) cudaFree(nf->stage.p);
+    for (cudaEvent_t e : nf->ev) cudaEventDestroy(e);
+    delete nf;
+}
+
+const char *nf_last_error(const nf_t *nf)
+{
+    if (!nf) return g_create_error.c_str();
+    return nf->last_error.c_str();
+}
+
+int nf_set_stream(nf_t *nf, void *stream)
+{
+    if (!nf) return NF_EINVAL;
+    nf->stream = static_cast<cudaStream_t>(stream);
+    return NF_OK;
+}
+
+int nf_set_accumulation(nf_t *nf, int mode)
+{
+    if (!nf) return NF_EINVAL;
+    if (mode != NF_ACC_COMPENSATED && mode != NF_ACC_PLAIN) return fail(nf, NF_EINVAL, "unknown accumulation mode");
+    nf->acc_mode = mode;
+    return NF_OK;
+}
+
+int nf_bin_particles(nf_t *nf, const double *xyz, int64_t n)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (n < 0 || n >= (1ll << 31) - 1) return fail(nf, NF_EINVAL, "n must satisfy 0 <= n < 2^31 - 1");
+    if (n > 0 && !xyz) return fail(nf, NF_EINVAL, "xyz is NULL");
+    if ((rc = ensure_capacity(nf, n))) return rc;
+    const double *dx = nullptr;
+    if (n > 0 && (rc = device_input(nf, 0, xyz, sizeof(double) * 3 * static_cast<size_t>(n),
+                                    reinterpret_cast<const void **>(&dx))))
+        return rc;
+    NF_CK(cudaMemsetAsync(nf->counts, 0, sizeof(int) * (static_cast<size_t>(nf->ncell) + 2), nf->stream));
+    NF_CK(cudaMemsetAsync(nf->err, 0, sizeof(int), nf->stream));
+    const int src = 1 - nf->cur;   // keep the live state untouched until the input is known to be valid
+    NF_CK(nf::bin_global(dx, static_cast<int>(n), nf->cpd, nf->inv_w, nf->keys[src], nf->vals[src], nf->xq_by_id,
+                         nf->counts, nf->err, nf->stream));
+    int herr = 0;
+    if ((rc = read_err(nf, &herr))) return rc;
+    if (herr) return fail(nf, NF_EINVAL, "non-finite or out-of-range position");
+    nf->n = n;
+    nf->have_particles = false;
+    nf->have_forces = false;
+    if (n > 0) {
+        if ((rc = sort_and_gather(nf, src, false))) return rc;
+    }
+    if ((rc = counts_to_cell_start(nf))) return rc;
+    NF_CK(cudaMemsetAsync(nf->vel, 0, sizeof(float4) * static_cast<size_t>(n < 1 ? 1 : n), nf->stream));
+    if ((rc = plan(nf))) return rc;
+    nf->box_dirty = true;
+    nf->generation = ++g_generation;
+    nf->have_particles = true;
+    NF_CK(cudaStreamSynchronize(nf->stream));
+    return NF_OK;
+}
+
+int nf_set_particles(nf_t *nf, const int64_t *cell_offsets, const int32_t *counts, const float *pos, int64_t n)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (n < 0 || n >= (1ll << 31) - 1) return fail(nf, NF_EINVAL, "n must satisfy 0 <= n < 2^31 - 1");
+    if (!cell_offsets || !counts || (n > 0 && !pos)) return fail(nf, NF_EINVAL, "NULL input");
+    if ((rc = ensure_capacity(nf, n))) return rc;
+    const size_t ob = sizeof(int64_t) * (static_cast<size_t>(nf->ncell) + 1);
+    const size_t cb = sizeof(int32_t) * static_cast<size_t>(nf->ncell);
+    const size_t pb = sizeof(float4) * static_cast<size_t>(n);
+    // stage all three inputs in one device buffer (each part 16-byte aligned)
+    const size_t o_off = 0, c_off = (ob + 15) & ~size_t(15), p_off = c_off + ((cb + 15) & ~size_t(15));
+    if ((rc = ensure_stage(nf, p_off + pb + 16))) return rc;
+    char *sp = static_cast<char *>(nf->stage.p);
+    NF_CK(cudaMemcpyAsync(sp + o_off, cell_offsets, ob, cudaMemcpyDefault, nf->stream));
+    NF_CK(cudaMemcpyAsync(sp + c_off, counts, cb, cudaMemcpyDefault, nf->stream));
+    if (n > 0) NF_CK(cudaMemcpyAsync(sp + p_off, pos, pb, cudaMemcpyDefault, nf->stream));
+    NF_CK(cudaMemsetAsync(nf->err, 0, sizeof(int), nf->stream));
+    // validated values go to scratch (offsets -> cell starts, xq_by_id -> positions)
+    NF_CK(nf::validate_loaded(reinterpret_cast<const int64_t *>(sp + o_off), reinterpret_cast<const int32_t *>(sp + c_off),
+                              reinterpret_cast<const float4 *>(sp + p_off), nf->ncell, static_cast<int>(n), nf->offsets,
+                              nf->xq_by_id, nf->err, nf->stream));
+    int herr = 0;
+    if ((rc = read_err(nf, &herr))) return rc;
+    if (herr) {
+        std::string why;
+        if (herr & 3) why += " offsets do not start at 0 / end at n;";
+        if (herr & 4) why += " negative count;";
+        if (herr & 8) why += " offsets are not the scan of counts;";
+        if (herr & 16) why += " offset out of range;";
+        if (herr & 32) why += " position non-finite or outside the cell;";
+        return fail(nf, NF_EINVAL, "nf_set_particles:" + why);
+    }
+    std::swap(nf->cell_start, nf->offsets);
+    std::swap(nf->pos, nf->xq_by_id);
+    nf->n = n;
+    NF_CK(nf::iota_u32(nf->vals[nf->cur], static_cast<int>(n), nf->stream));
+    NF_CK(nf::fill_cell_ids(nf->cell_start, nf->ncell, static_cast<int>(n), nf->keys[nf->cur], nf->stream));
+    NF_CK(cudaMemsetAsync(nf->vel, 0, sizeof(float4) * static_cast<size_t>(n < 1 ? 1 : n), nf->stream));
+    if ((rc = plan(nf))) return rc;
+    nf->box_dirty = true;
+    nf->generation = ++g_generation;
+    nf->have_particles = true;
+    nf->have_forces = false;
+    NF_CK(cudaStreamSynchronize(nf->stream));
+    return NF_OK;
+}
+
+int nf_set_velocities(nf_t *nf, const float *vel)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
+    if (nf->n == 0) return NF_OK;
+    if (!vel) return fail(nf, NF_EINVAL, "vel is NULL");
+    NF_CK(cudaMemcpyAsync(nf->vel, vel, sizeof(float4) * static_cast<size_t>(nf->n), cudaMemcpyDefault, nf->stream));
+    return NF_OK;
+}
+
+int nf_get_particles(nf_t *nf, int64_t *cell_offsets, int32_t *counts, float *pos, float *vel, int64_t *perm)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
+    const int ncell = nf->ncell;
+    const int n = static_cast<int>(nf->n);
+    cudaStream_t st = nf->stream;
+    if (cell_offsets) {
+        rc = produce_out(nf, cell_offsets, sizeof(int64_t) * (static_cast<size_t>(ncell) + 1), [&](void *d) -> int {
+            k_offsets64<<<nblk(static_cast<int64_t>(ncell) + 1), 256, 0, st>>>(nf->cell_start, ncell,
+                                                                                static_cast<int64_t *>(d));
+            NF_CK(cudaGetLastError());
+            return NF_OK;
+        });
+        if (rc) return rc;
+    }
+    if (counts) {
+        rc = produce_out(nf, counts, sizeof(int32_t) * static_cast<size_t>(ncell), [&](void *d) -> int {
+            k_counts32<<<nblk(ncell), 256, 0, st>>>(nf->cell_start, ncell, static_cast<int32_t *>(d));
+            NF_CK(cudaGetLastError());
+            return NF_OK;
+        });
+        if (rc) return rc;
+    }
+    if (pos && n > 0) NF_CK(cudaMemcpyAsync(pos, nf->pos, sizeof(float4) * n, cudaMemcpyDefault, st));
+    if (vel && n > 0) NF_CK(cudaMemcpyAsync(vel, nf->vel, sizeof(float4) * n, cudaMemcpyDefault, st));
+    if (perm && n > 0) {
+        rc = produce_out(nf, perm, sizeof(int64_t) * n, [&](void *d) -> int {
+            k_perm64<<<nblk(n), 256, 0, st>>>(nf->vals[nf->cur], n, static_cast<int64_t *>(d));
+            NF_CK(cudaGetLastError());
+            return NF_OK;
+        });
+        if (rc) return rc;
+    }
+    NF_CK(cudaStreamSynchronize(st));
+    return NF_OK;
+}
+
+int nf_num_particles(const nf_t *nf, int64_t *n)
+{
+    if (!nf || !n) return NF_EINVAL;
+    *n = nf->n;
+    return NF_OK;
+}
+
+int nf_pair_count(nf_t *nf, int64_t *pairs)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (!pairs) return fail(nf, NF_EINVAL, "pairs is NULL");
+    if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
+    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->pairs, nf->counts, nf->offsets, nf->stream));
+    unsigned long long h = 0;
+    NF_CK(cudaMemcpyAsync(&h, nf->pairs, sizeof(h), cudaMemcpyDeviceToHost, nf->stream));
+    NF_CK(cudaStreamSynchronize(nf->stream));
+    *pairs = static_cast<int64_t>(h);
+    return NF_OK;
+}
+
+int nf_forces(nf_t *nf, float *acc)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
+    const size_t bytes = sizeof(float4) * static_cast<size_t>(nf->n);
+    float4 *out = nullptr;
+    bool copy_back = false;
+    if (acc && nf->n > 0) {
+        if (is_device_cached(nf, 1, acc) && aligned16(acc)) {
+            out = reinterpret_cast<float4 *>(acc);
+        } else {
+            if (!nf->acc32 && (rc = dalloc(nf, &nf->acc32, sizeof(float4) * static_cast<size_t>(nf->cap)))) return rc;
+            out = nf->acc32;
+            copy_back = true;
+        }
+    }
+    if ((rc = upload_box(nf, out, nf->acc64, nullptr))) return rc;
+    if (nf->n > 0 && (rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
+    if (copy_back) NF_CK(cudaMemcpyAsync(acc, nf->acc32, bytes, cudaMemcpyDefault, nf->stream));
+    nf->have_forces = true;
+    return NF_OK;
+}
+
+int nf_get_forces64(nf_t *nf, double *acc)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (!nf->have_forces) return fail(nf, NF_ESTATE, "no forces computed");
+    if (!acc) return fail(nf, NF_EINVAL, "acc is NULL");
+    if (nf->n > 0)
+        NF_CK(cudaMemcpyAsync(acc, nf->acc64, 3 * sizeof(double) * static_cast<size_t>(nf->n), cudaMemcpyDefault,
+                              nf->stream));
+    return NF_OK;
+}
+
+int nf_vjp(nf_t *nf, const float *w, float *grad)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
+    if (nf->n == 0) return NF_OK;
+    if (!w || !grad) return fail(nf, NF_EINVAL, "NULL input");
+    const size_t bytes = sizeof(float4) * static_cast<size_t>(nf->n);
+    const float4 *cot = nullptr;
+    if (is_device_cached(nf, 2, w) && aligned16(w)) {
+        cot = reinterpret_cast<const float4 *>(w);
+    } else {
+        if (!nf->cot && (rc = dalloc(nf, &nf->cot, sizeof(float4) * static_cast<size_t>(nf->cap)))) return rc;
+        NF_CK(cudaMemcpyAsync(nf->cot, w, bytes, cudaMemcpyDefault, nf->stream));
+        cot = nf->cot;
+    }
+    float4 *out = nullptr;
+    bool copy_back = false;
+    if (is_device_cached(nf, 3, grad) && aligned16(grad)) {
+        out = reinterpret_cast<float4 *>(grad);
+    } else {
+        if (!nf->acc32 && (rc = dalloc(nf, &nf->acc32, sizeof(float4) * static_cast<size_t>(nf->cap)))) return rc;
+        out = nf->acc32;
+        copy_back = true;
+    }
+    if ((rc = upload_box(nf, out, nullptr, cot))) return rc;
+    if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 1))) return rc;
+    if (copy_back) NF_CK(cudaMemcpyAsync(grad, nf->acc32, bytes, cudaMemcpyDefault, nf->stream));
+    return NF_OK;
+}
+
+int nf_kick_drift(nf_t *nf, double dt)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (!nf->have_forces) return fail(nf, NF_ESTATE, "nf_kick_drift needs a previous nf_forces");
+    if (!std::isfinite(dt)) return fail(nf, NF_EINVAL, "dt must be finite");
+    const int n = static_cast<int>(nf->n);
+    if (n == 0) return NF_OK;
+    NF_CK(cudaMemsetAsync(nf->err, 0, sizeof(int), nf->stream));
+    NF_CK(nf::kick(nf->vel, nf->acc64, dt, nf->inv_w, n, nf->vel_tmp, nf->err, nf->stream));
+    int viol = 0;
+    if ((rc = read_err(nf, &viol))) return rc;
+    if (viol)
+        return fail(nf, NF_EINVAL, std::to_string(viol) + " particles would drift more than 0.8 cell widths");
+    const int src = 1 - nf->cur;
+    NF_CK(nf::drift(nf->pos, nf->vel_tmp, nf->keys[nf->cur], nf->vals[nf->cur], dt, nf->inv_w, nf->cpd, n,
+                    nf->keys[src], nf->vals[src], nf->xq_by_id, nf->vel_by_id, nf->stream));
+    NF_CK(cudaMemsetAsync(nf->counts, 0, sizeof(int) * (static_cast<size_t>(nf->ncell) + 2), nf->stream));
+    NF_CK(nf::count_keys(nf->keys[src], n, nf->counts, nf->stream));
+    if ((rc = sort_and_gather(nf, src, true))) return rc;
+    if ((rc = counts_to_cell_start(nf))) return rc;
+    if ((rc = plan(nf))) return rc;
+    nf->box_dirty = true;
+    nf->generation = ++g_generation;
+    nf->have_forces = false;
+    NF_CK(cudaStreamSynchronize(nf->stream));
+    return NF_OK;
+}
+
+int nf_profile(nf_t *nf, int enable)
+{
+    if (!nf) return NF_EINVAL;
+    nf->profile = enable != 0;
+    return NF_OK;
+}
+
+int nf_profile_read(nf_t *nf, int64_t *launches, double *ms)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    NF_CK(cudaStreamSynchronize(nf->stream));
+    double total = 0;
+    for (size_t k = 0; k + 1 < nf->ev_used; k += 2) {
+        float t = 0;
+        NF_CK(cudaEventElapsedTime(&t, nf->ev[k], nf->ev[k + 1]));
+        total += t;
+    }
+    if (launches) *launches = static_cast<int64_t>(nf->ev_used / 2);
+    if (ms) *ms = total;
+    nf->ev_used = 0;
+    return NF_OK;
+}
+
+int nf_set_shape(nf_t *nf, int warps, int stage)
+{
+    if (!nf) return NF_EINVAL;
+    if (warps < 1 || warps > 8 || (stage != 128 && stage != 256))
+        return fail(nf, NF_EINVAL, "warps must be 1..8 and stage 128 or 256");
+    nf->shape.warps = warps;
+    nf->shape.stage = stage;
+    return NF_OK;
+}
+
+int nf_tune(nf_t *nf, char *report, int report_len)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
+    char key[160];
+    cudaDeviceProp prop;
+    NF_CK(cudaGetDeviceProperties(&prop, nf->device));
+    std::snprintf(key, sizeof(key), "%s|cpd=%d|n=%lld|acc=%d", prop.name, nf->cpd, static_cast<long long>(nf->n),
+                  nf->acc_mode);
+    std::string summary;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            nf->shape = it->second;
+            summary = "cached";
+        }
+    }
+    if (summary.empty() && nf->n > 0) {
+        const PairShape cand[] = {{4, 128, 0}, {8, 128, 0}, {4, 256, 0}, {8, 256, 0}, {2, 128, 0}};
+        cudaEvent_t a, b;
+        NF_CK(cudaEventCreate(&a));
+        NF_CK(cudaEventCreate(&b));
+        float best = 1e30f;
+        PairShape best_s = nf->shape;
+        const bool prof = nf->profile;
+        nf->profile = false;
+        if ((rc = upload_box(nf, nullptr, nf->acc64, nullptr))) return rc;
+        for (const PairShape &s : cand) {
+            if (nf::pair_max_blocks_per_sm(nf->acc_mode == NF_ACC_COMPENSATED, 0, s) < 1) continue;
+            nf->shape = s;
+            if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
+            NF_CK(cudaEventRecord(a, nf->stream));
+            for (int r = 0; r < 2; ++r)
+                if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
+            NF_CK(cudaEventRecord(b, nf->stream));
+            NF_CK(cudaEventSynchronize(b));
+            float t = 0;
+            NF_CK(cudaEventElapsedTime(&t, a, b));
+            char part[96];
+            std::snprintf(part, sizeof(part), "%dx%d:%.3fms ", s.warps, s.stage, t / 2);
+            summary += part;
+            if (t < best) {
+                best = t;
+                best_s = s;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        nf->profile = prof;
+        nf->shape = best_s;
+        nf->have_forces = true;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best_s;
+        char part[64];
+        std::snprintf(part, sizeof(part), "-> %dx%d", best_s.warps, best_s.stage);
+        summary += part;
+    }
+    if (report && report_len > 0) std::snprintf(report, static_cast<size_t>(report_len), "%s", summary.c_str());
+    return NF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batched
+
+namespace {
+
+struct Batch {
+    std::vector<nf_t *> boxes;
+    std::vector<uint64_t> gens;
+    std::vector<BoxDev> h_desc;
+    BoxDev *d_desc = nullptr;
+    Item *items = nullptr;
+    int64_t item_cap = 0;
+    int *n_items = nullptr, *queue = nullptr;
+    int device = -1;
+};
+
+std::mutex g_batch_mu;
+Batch g_batch;
+
+}  // namespace
+
+void batch_forget(nf_t *nf)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (nf_t *b : g_batch.boxes)
+        if (b == nf) {
+            g_batch.boxes.clear();
+            g_batch.gens.clear();
+            return;
+        }
+}
+
+namespace {
+
+void batch_release(Batch &b)
+{
+    if (b.d_desc) cudaFree(b.d_desc);
+    if (b.items) cudaFree(b.items);
+    if (b.n_items) cudaFree(b.n_items);
+    if (b.queue) cudaFree(b.queue);
+    b = Batch();
+}
+
+}  // namespace
+
+extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc)
+{
+    if (!boxes || nbox < 1 || nbox > 4096) return NF_EINVAL;
+    nf_t *nf = boxes[0];
+    int rc = check_box(nf);
+    if (rc) return rc;
+    for (int b = 0; b < nbox; ++b) {
+        if (!boxes[b]) return fail(nf, NF_EINVAL, "NULL box");
+        if (!boxes[b]->have_particles) return fail(nf, NF_ESTATE, "box without particles");
+        if (boxes[b]->device != nf->device) return fail(nf, NF_EINVAL, "boxes on different devices");
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    Batch &B = g_batch;
+    bool same = B.device == nf->device && static_cast<int>(B.boxes.size()) == nbox;
+    for (int b = 0; same && b < nbox; ++b) same = B.boxes[b] == boxes[b] && B.gens[b] == boxes[b]->generation;
+    if (!same) {
+        // (re)plan: one item list over all boxes, class-major (largest cells first)
+        cudaStreamSynchronize(nf->stream);
+        int64_t need = 16;
+        for (int b = 0; b < nbox; ++b) need += boxes[b]->item_cap;
+        if (B.device != nf->device || need > B.item_cap || static_cast<int>(B.h_desc.size()) < nbox) {
+            batch_release(B);
+            if ((rc = dalloc(nf, &B.items, sizeof(Item) * static_cast<size_t>(need))) ||
+                (rc = dalloc(nf, &B.d_desc, sizeof(BoxDev) * static_cast<size_t>(nbox))) ||
+                (rc = dalloc(nf, &B.n_items, sizeof(int) * 4)) || (rc = dalloc(nf, &B.queue, sizeof(int) * 4))) {
+                batch_release(B);
+                return rc;
+            }
+            B.item_cap = need;
+            B.device = nf->device;
+            B.h_desc.assign(nbox, BoxDev{});
+        }
+        NF_CK(nf::zero_device_int(B.n_items, nf->stream));
+        for (int cls = 0; cls < nf::kClasses; ++cls)
+            for (int b = 0; b < nbox; ++b)
+                NF_CK(nf::plan_items_class(boxes[b]->cell_start, boxes[b]->ncell, b, cls, B.items, B.n_items,
+                                           boxes[b]->counts, boxes[b]->offsets, boxes[b]->scan_tmp, nf->stream));
+        B.boxes.assign(boxes, boxes + nbox);
+        B.gens.resize(nbox);
+        for (int b = 0; b < nbox; ++b) B.gens[b] = boxes[b]->generation;
+        std::fill(B.h_desc.begin(), B.h_desc.end(), BoxDev{});
+        B.h_desc.resize(nbox);
+        NF_CK(cudaMemsetAsync(B.d_desc, 0, sizeof(BoxDev) * nbox, nf->stream));
+    }
+    // descriptors (uploaded only when an output pointer changed)
+    bool dirty = false;
+    std::vector<int> copy_back(nbox, 0);
+    for (int b = 0; b < nbox; ++b) {
+        nf_t *x = boxes[b];
+        float4 *out = nullptr;
+        float *a = acc ? acc[b] : nullptr;
+        if (a && x->n > 0) {
+            if (is_device_cached(x, 1, a) && aligned16(a)) {
+                out = reinterpret_cast<float4 *>(a);
+            } else {
+                if (!x->acc32 && (rc = dalloc(x, &x->acc32, sizeof(float4) * static_cast<size_t>(x->cap)))) return rc;
+                out = x->acc32;
+                copy_back[b] = 1;
+            }
+        }
+        BoxDev d{};
+        fill_box_desc(x, d, out, x->acc64, nullptr);
+        if (std::memcmp(&d, &B.h_desc[b], sizeof(BoxDev)) != 0) {
+            B.h_desc[b] = d;
+            dirty = true;
+        }
+    }
+    if (dirty)
+        NF_CK(cudaMemcpyAsync(B.d_desc, B.h_desc.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice, nf->stream));
+    if ((rc = launch_forces(nf, B.d_desc, B.items, B.n_items, B.queue, 0))) return rc;
+    for (int b = 0; b < nbox; ++b) {
+        boxes[b]->have_forces = true;
+        if (copy_back[b])
+            NF_CK(cudaMemcpyAsync(acc[b], boxes[b]->acc32, sizeof(float4) * static_cast<size_t>(boxes[b]->n),
+                                  cudaMemcpyDefault, nf->stream));
+    }
+    return NF_OK;
+}

@@ -403,35 +403,51 @@ size_t smem_bytes(int warps)
     return static_cast<size_t>(warps) * ((ADJ ? 4 : 2) * B * sizeof(float4) + 256 * sizeof(int));
 }
 
+// Occupancy of one instantiation at `warps` warps per block, computed once
+// (the dynamic shared-memory limit is raised once to the 8-warp size), so a
+// launch makes no attribute or occupancy query and can be stream-captured.
+template <int B, bool COMP, bool ADJ>
+int blocks_per_sm(int warps)
+{
+    static int cache[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+    static bool attr = false;
+    auto kern = pair_kernel<B, COMP, ADJ>;
+    if (!attr) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem_bytes<B, COMP, ADJ>(8))) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        attr = true;
+    }
+    if (cache[warps] < 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem_bytes<B, COMP, ADJ>(warps)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cache[warps] = per_sm;
+    }
+    return cache[warps];
+}
+
 template <int B, bool COMP, bool ADJ>
 cudaError_t launch_t(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, PairShape shape,
                      int sm_count, cudaStream_t st)
 {
-    auto kern = pair_kernel<B, COMP, ADJ>;
-    const size_t smem = smem_bytes<B, COMP, ADJ>(shape.warps);
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (err != cudaSuccess) return err;
-    int blocks = shape.blocks;
-    if (blocks <= 0) {
-        int per_sm = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, shape.warps * 32, smem);
-        if (err != cudaSuccess) return err;
-        blocks = sm_count * (per_sm > 0 ? per_sm : 1);
-    }
-    kern<<<blocks, shape.warps * 32, smem, st>>>(boxes, items, n_items, queue);
+    const int per_sm = blocks_per_sm<B, COMP, ADJ>(shape.warps);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int blocks = shape.blocks > 0 ? shape.blocks : sm_count * per_sm;
+    pair_kernel<B, COMP, ADJ><<<blocks, shape.warps * 32, smem_bytes<B, COMP, ADJ>(shape.warps), st>>>(boxes, items,
+                                                                                                      n_items, queue);
     return cudaGetLastError();
 }
 
 template <int B, bool COMP, bool ADJ>
 int max_blocks_t(PairShape shape)
 {
-    int per_sm = 0;
-    auto kern = pair_kernel<B, COMP, ADJ>;
-    const size_t smem = smem_bytes<B, COMP, ADJ>(shape.warps);
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, shape.warps * 32, smem) != cudaSuccess) return 0;
-    return per_sm;
+    return blocks_per_sm<B, COMP, ADJ>(shape.warps);
 }
 
 }  // namespace

@@ -1,0 +1,261 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Indexing (cells, offsets, order, quantised positions) must be bit-exact;
+forces must meet the rms relative error and max-error bound of the FP32 path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import generators as gen
+from synth import workload
+from tests.gpu_helpers import (BOUND_K, RMS_TOL, RMS_TOL_PLAIN, make_box, oracle_side, require_cuda,
+                               sample_sinks)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    require_cuda()
+    from paper_1810_02916_b300 import build
+    build.build()
+
+
+def _assert_same_layout(nf, b):
+    st = nf.get_particles()
+    assert np.array_equal(st["cell_offsets"], b.offsets)
+    assert np.array_equal(st["counts"].astype(np.int64), b.counts)
+    assert np.array_equal(st["perm"], b.order)
+    assert np.array_equal(st["pos"][:, :3], b.xq)
+    assert np.all(st["pos"][:, 3] == 0)
+    return st
+
+
+def _check_forces(acc, ref, sa, tol=RMS_TOL, k=BOUND_K):
+    s = oracle.error_stats(acc[:, :3], ref, sa)
+    assert s["rms_rel"] <= tol, s
+    assert s["max_bound_ratio"] <= k, s
+    return s
+
+
+# ------------------------------------------------------------------ indexing
+
+@pytest.mark.parametrize("case", ["uniform32k", "clustered", "edges"])
+def test_binning_is_bit_exact(case):
+    rng = np.random.default_rng(1)
+    if case == "uniform32k":
+        w = workload("uniform32k")
+        X, cpd = w.pos, w.cpd
+    elif case == "clustered":
+        X, _ = gen.clustered(60000, rng, 5, 0.5 / 12, 3.0 / 12)
+        cpd = 12
+    else:
+        cpd = 7
+        X = rng.random((5000, 3))
+        X[:300] = np.floor(X[:300] * cpd) / cpd               # on cell faces
+        X[300:320] = np.nextafter(1.0, 0.0)                   # just below the box edge
+        X[320:340] = -1e-9                                    # wraps to the last cell
+        X[340:360] = 1.0                                      # wraps to the first cell
+        X[360:2000] = X[360]                                  # one crowded cell, order by id
+        X[2000:2100] = 5.3                                    # far outside: periodic wrap
+    nf = make_box(X, cpd, 1e-4)
+    _assert_same_layout(nf, oracle_side(X, cpd))
+
+
+def test_pair_count_matches_oracle():
+    X, _ = gen.clustered(80000, np.random.default_rng(2), 6, 0.5 / 15, 3.0 / 15)
+    nf = make_box(X, 15, 1e-4)
+    assert nf.pair_count() == oracle.pair_count(oracle_side(X, 15))
+
+
+# ------------------------------------------------------------------ forces
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["compensated", "plain"])
+def test_uniform32k_all_sinks(mode):
+    w = workload("uniform32k")
+    nf = make_box(w.pos, w.cpd, w.eps, mode=mode)
+    b = oracle_side(w.pos, w.cpd)
+    _assert_same_layout(nf, b)
+    acc = nf.forces()
+    ref, sa, pairs = oracle.forces(b, w.eps, with_sumabs=True)
+    assert nf.pair_count() == pairs
+    _check_forces(acc, ref, sa, tol=RMS_TOL if mode == 0 else RMS_TOL_PLAIN)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["compensated", "plain"])
+def test_clustered64_all_sinks(mode):
+    w = workload("clustered64")
+    nf = make_box(w.pos, w.cpd, w.eps, mode=mode)
+    b = oracle_side(w.pos, w.cpd)
+    acc = nf.forces()
+    ref, sa, _ = oracle.forces(b, w.eps, with_sumabs=True)
+    _check_forces(acc, ref, sa, tol=RMS_TOL if mode == 0 else RMS_TOL_PLAIN)
+    f64 = nf.forces64()
+    assert np.array_equal(f64.astype(np.float32), acc[:, :3])
+
+
+def test_every_tile_shape_and_ragged_tails():
+    """Cells of 1..300 particles (split mode, 1/2/4 sinks per lane, several tiles, ragged tails)."""
+    cpd = 9
+    rng = np.random.default_rng(3)
+    parts = []
+    for c in range(cpd ** 3):
+        k = c % 41 if c < 600 else (129 + c % 172)
+        cx, cy, cz = c // (cpd * cpd), (c // cpd) % cpd, c % cpd
+        parts.append((np.array([cx, cy, cz]) + rng.random((k, 3))) / cpd)
+    X = np.concatenate(parts)
+    X = X[rng.permutation(len(X))]
+    eps = 0.3 / cpd
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    _assert_same_layout(nf, b)
+    acc = nf.forces()
+    ref, sa, _ = oracle.forces(b, eps, with_sumabs=True)
+    _check_forces(acc, ref, sa)
+
+
+def test_one_dense_cell_many_tiles():
+    """A 6000-particle cell (largest occupancy class) amid sparse cells."""
+    cpd = 6
+    rng = np.random.default_rng(4)
+    X = np.concatenate([rng.random((3000, 3)), (np.array([2, 3, 1]) + 0.5 + 0.1 * rng.standard_normal((6000, 3))) / cpd])
+    X = np.mod(X, 1.0)
+    eps = 0.05 / cpd
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    assert b.counts.max() >= 4096
+    acc = nf.forces()
+    ref, sa, _ = oracle.forces(b, eps, with_sumabs=True)
+    _check_forces(acc, ref, sa)
+
+
+def test_cpd5_every_pair_once_against_bruteforce():
+    cpd = 5
+    X, _ = gen.clustered(3000, np.random.default_rng(5), 3, 0.1, 0.3)
+    eps = 0.01
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    acc = nf.forces()
+    brute = oracle.bruteforce(b, eps)
+    _, sa, _ = oracle.forces(b, eps, with_sumabs=True)
+    _check_forces(acc, brute, sa)
+
+
+def test_degenerate_inputs():
+    # empty box
+    nf = make_box(np.zeros((0, 3)), 5, 0.01)
+    assert nf.forces().shape == (0, 4)
+    assert nf.pair_count() == 0
+    # one particle: no force
+    nf = make_box(np.array([[0.3, 0.6, 0.9]]), 5, 0.01)
+    assert np.all(nf.forces() == 0)
+    # coincident distinct particles: F(0) = 0, no NaN; plus an exact two-body pair
+    X = np.array([[0.5, 0.5, 0.5], [0.5, 0.5, 0.5], [0.1, 0.1, 0.1], [0.1, 0.1, 0.13]])
+    nf = make_box(X, 5, 0.01)
+    acc = nf.forces()
+    b = oracle_side(X, 5)
+    ref = oracle.forces(b, 0.01)
+    assert np.all(np.isfinite(acc))
+    assert np.allclose(acc[:, :3], ref, rtol=2e-6, atol=0)
+    # a particle exactly at a cell corner and its neighbour across the periodic boundary
+    X = np.array([[0.0, 0.0, 0.0], [1.0 - 1e-3, 1.0 - 1e-3, 1.0 - 1e-3]])
+    nf = make_box(X, 7, 1e-4)
+    acc = nf.forces()
+    ref = oracle.forces(oracle_side(X, 7), 1e-4)
+    assert np.allclose(acc[:, :3], ref, rtol=2e-6, atol=0)
+
+
+# ------------------------------------------------------------------ invariants
+
+def test_whole_cell_translation_is_bit_identical():
+    cpd = 8
+    X, _ = gen.clustered(40000, np.random.default_rng(6), 4, 0.05, 0.2)
+    X = np.floor(X * 2.0 ** 30) * 2.0 ** -30          # dyadic: the shift below is exact
+    nf = make_box(X, cpd, 1e-3)
+    b = oracle_side(X, cpd)
+    a0 = nf.forces()
+    shift = np.array([3, 1, 6]) / cpd
+    X2 = np.mod(X + shift, 1.0)
+    b2 = oracle_side(X2, cpd)
+    # same particles must keep their cell-relative offsets for the test to apply
+    assert np.array_equal(b2.xq[np.argsort(b2.order)], b.xq[np.argsort(b.order)])
+    nf2 = make_box(X2, cpd, 1e-3)
+    a1 = nf2.forces()
+    # map by particle id
+    assert np.array_equal(a1[np.argsort(b2.order)], a0[np.argsort(b.order)])
+
+
+def test_third_law_on_gpu():
+    X, _ = gen.clustered(50000, np.random.default_rng(7), 5, 0.05, 0.2)
+    nf = make_box(X, 10, 1e-3)
+    b = oracle_side(X, 10)
+    nf.forces(False)
+    a64 = nf.forces64()
+    _, sa, _ = oracle.forces(b, 1e-3, with_sumabs=True)
+    assert np.abs(a64.sum(axis=0)).max() <= 64 * 2.0 ** -24 * sa.sum()
+
+
+def test_lattice_zero_on_gpu():
+    cpd = 9
+    g = (np.arange(cpd) + 0.5) / cpd
+    X = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3) + np.array([0.1, 0.2, -0.3]) / cpd
+    nf = make_box(X, cpd, 0.01 / cpd)
+    acc = nf.forces()
+    _, sa, _ = oracle.forces(oracle_side(X, cpd), 0.01 / cpd, with_sumabs=True)
+    assert np.abs(acc[:, :3]).max() <= 8 * 2.0 ** -24 * sa.max()
+
+
+# ------------------------------------------------------------------ state, validation
+
+def test_checkpoint_resume_is_bit_identical():
+    import paper_1810_02916_b300 as nfb
+    X, _ = gen.clustered(30000, np.random.default_rng(8), 3, 0.05, 0.2)
+    nf = make_box(X, 9, 1e-3)
+    a0 = nf.forces()
+    st = nf.get_particles()
+    nf2 = nfb.NearField(9, 1e-3)
+    nf2.set_particles(st["cell_offsets"], st["counts"], st["pos"])
+    assert np.array_equal(nf2.forces(), a0)
+
+
+def test_set_particles_rejects_bad_input_and_keeps_state():
+    import paper_1810_02916_b300 as nfb
+    X, _ = gen.clustered(5000, np.random.default_rng(9), 2, 0.05, 0.2)
+    nf = make_box(X, 6, 1e-3)
+    a0 = nf.forces()
+    st = nf.get_particles()
+    bad = st["cell_offsets"].copy()
+    bad[5] += 1
+    with pytest.raises(nfb.NearFieldError) as e:
+        nf.set_particles(bad, st["counts"], st["pos"])
+    assert e.value.code == nfb.NF_EINVAL
+    pos = st["pos"].copy()
+    pos[7, 1] = 0.75
+    with pytest.raises(nfb.NearFieldError):
+        nf.set_particles(st["cell_offsets"], st["counts"], pos)
+    pos[7, 1] = np.nan
+    with pytest.raises(nfb.NearFieldError):
+        nf.set_particles(st["cell_offsets"], st["counts"], pos)
+    with pytest.raises(nfb.NearFieldError):
+        nf.bin_particles(np.full((10, 3), np.inf))
+    assert np.array_equal(nf.forces(), a0)
+
+
+def test_kick_drift_requires_forces_and_respects_drift_limit():
+    import paper_1810_02916_b300 as nfb
+    X = np.random.default_rng(10).random((2000, 3))
+    nf = make_box(X, 7, 1e-3)
+    with pytest.raises(nfb.NearFieldError) as e:
+        nf.kick_drift(0.01)
+    assert e.value.code == nfb.NF_ESTATE
+    nf.forces(False)
+    st0 = nf.get_particles()
+    v = np.zeros((nf.n, 4), np.float32)
+    v[3, 0] = 1.0                      # moves 1.0 * dt * 7 cells
+    nf.set_velocities(v)
+    with pytest.raises(nfb.NearFieldError) as e:
+        nf.kick_drift(0.2)
+    assert e.value.code == nfb.NF_EINVAL
+    st1 = nf.get_particles()
+    assert np.array_equal(st0["pos"], st1["pos"]) and np.array_equal(st0["perm"], st1["perm"])

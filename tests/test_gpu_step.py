@@ -1,0 +1,239 @@
+"""GPU parity of the rest of the path: kick-drift with re-binning, the adjoint
+(and its autograd wrapper), the batched persistent launch (also under a
+captured CUDA graph), the launch-shape tuner, and sampled parity at the full
+workload sizes."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import generators as gen
+from synth import workload
+from tests.gpu_helpers import BOUND_K, RMS_TOL, make_box, oracle_side, require_cuda, sample_sinks
+
+pytestmark = pytest.mark.gpu
+
+VJP_RMS_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    require_cuda()
+    from paper_1810_02916_b300 import build
+    build.build()
+
+
+def _global_by_id(st, cpd, box=1.0):
+    C = cpd
+    counts = st["counts"].astype(np.int64)
+    cell = np.repeat(np.arange(C ** 3), counts)
+    xyz = np.stack([cell // (C * C), (cell // C) % C, cell % C], axis=1).astype(np.float64)
+    X = (xyz + 0.5 + st["pos"][:, :3].astype(np.float64)) * (box / C)
+    out = np.empty_like(X)
+    out[st["perm"]] = X
+    v = np.empty((len(X), 3))
+    v[st["perm"]] = st["vel"][:, :3]
+    return out, v
+
+
+def _min_image(d, box=1.0):
+    return d - box * np.round(d / box)
+
+
+# ------------------------------------------------------------------ kick / drift
+
+def test_one_kick_drift_step_matches_oracle():
+    cpd, eps = 8, 2e-3
+    rng = np.random.default_rng(21)
+    X, _ = gen.clustered(20000, rng, 4, 0.05, 0.2)
+    w = 1.0 / cpd
+    dt = 1e-3
+    V = (rng.standard_normal((len(X), 3)) * 0.1 * w / dt).astype(np.float32)
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    vel = np.zeros((nf.n, 4), np.float32)
+    vel[:, :3] = V[b.order]
+    nf.set_velocities(vel)
+    nf.forces(False)
+    nf.kick_drift(dt)
+    Xg, Vg = _global_by_id(nf.get_particles(), cpd)
+    # oracle: FP64 forces on the same quantised start, FP64 kick and drift, re-binned
+    A = np.empty((len(X), 3))
+    A[b.order] = oracle.forces(b, eps)
+    X0 = np.empty((len(X), 3))
+    X0[b.order] = oracle.global_positions(b)
+    X1, V1 = oracle.kick_drift(X0, V.astype(np.float64), A, dt, 1.0)
+    b1 = oracle.bin_positions(X1, cpd)
+    X1q = np.empty_like(X1)
+    X1q[b1.order] = oracle.global_positions(b1)
+    # velocities: FP32 storage (2^-24 relative) plus the FP32 force error times dt
+    vtol = 2.0 ** -23 * np.abs(V1) + 1e-5 * np.abs(A).max() * dt
+    assert np.all(np.abs(Vg - V1) <= vtol)
+    # positions: one quantum of the 2^-22 grid on each side plus the velocity error times dt
+    q = 2.0 ** -22 * w
+    ptol = 2 * q + vtol * dt
+    assert np.all(np.abs(_min_image(Xg - X1q)) <= ptol + 1e-15)
+
+
+def test_ten_steps_track_the_oracle_trajectory():
+    """Ten leapfrog steps of a smooth system stay within a small multiple of the grid quantum."""
+    cpd, eps = 6, 0.3 / 6
+    rng = np.random.default_rng(22)
+    X = rng.random((6000, 3))
+    dt = 2e-4
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    Xo = np.empty_like(X)
+    Xo[b.order] = oracle.global_positions(b)
+    Vo = np.zeros_like(X)
+    for _ in range(10):
+        nf.forces(False)
+        nf.kick_drift(dt)
+        bo = oracle.bin_positions(Xo, cpd)
+        A = np.empty_like(X)
+        A[bo.order] = oracle.forces(bo, eps)
+        Xo, Vo = oracle.kick_drift(Xo, Vo, A, dt, 1.0)
+    Xg, _ = _global_by_id(nf.get_particles(), cpd)
+    err = np.abs(_min_image(Xg - Xo)).max() * cpd
+    assert err < 1e-4, err      # in cell widths
+
+
+def test_kick_drift_keeps_canonical_order():
+    """After a drift the layout equals a fresh binning of the drifted particles."""
+    import paper_1810_02916_b300 as nfb
+    cpd = 8                          # power of two: global <-> cell coordinates are exact
+    rng = np.random.default_rng(23)
+    X = rng.random((30000, 3))
+    nf = make_box(X, cpd, 1e-3)
+    vel = np.zeros((nf.n, 4), np.float32)
+    vel[:, :3] = rng.standard_normal((nf.n, 3)).astype(np.float32) * 0.3
+    nf.set_velocities(vel)
+    nf.forces(False)
+    nf.kick_drift(0.05)
+    st = nf.get_particles()
+    Xg, _ = _global_by_id(st, cpd)
+    nf2 = nfb.NearField(cpd, 1e-3)
+    nf2.bin_particles(Xg)
+    st2 = nf2.get_particles()
+    assert np.array_equal(st["cell_offsets"], st2["cell_offsets"])
+    assert np.array_equal(st["pos"], st2["pos"])
+    assert np.array_equal(st["perm"], st2["perm"])
+
+
+# ------------------------------------------------------------------ adjoint
+
+def test_vjp_matches_oracle_gradient():
+    w = workload("clustered64")
+    nf = make_box(w.pos, w.cpd, w.eps)
+    b = oracle_side(w.pos, w.cpd)
+    rng = np.random.default_rng(24)
+    W = np.zeros((nf.n, 4), np.float32)
+    W[:, :3] = gen.cotangent(nf.n, rng).astype(np.float32)
+    g = nf.vjp(W)
+    sinks = sample_sinks(b, 20000)
+    ref = oracle.vjp(b, w.eps, W[:, :3].astype(np.float64), sinks)
+    s = oracle.error_stats(g[sinks, :3], ref)
+    assert s["rms_rel"] <= VJP_RMS_TOL, s
+
+
+def test_autograd_function_backward_is_the_adjoint():
+    torch = require_cuda()
+    from paper_1810_02916_b300.autograd import nearfield_forces
+    cpd, eps = 8, 2e-3
+    X, _ = gen.clustered(20000, np.random.default_rng(25), 3, 0.05, 0.2)
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    st = nf.get_particles()
+    pos = torch.tensor(st["pos"], device="cuda", requires_grad=True)
+    offs = torch.tensor(st["cell_offsets"], device="cuda")
+    cnts = torch.tensor(st["counts"], device="cuda")
+    W = torch.zeros((nf.n, 4), device="cuda")
+    W[:, :3] = torch.tensor(gen.cotangent(nf.n, np.random.default_rng(26)), dtype=torch.float32)
+    acc = nearfield_forces(pos, nf, offs, cnts)
+    (acc * W).sum().backward()
+    ref_acc, sa, _ = oracle.forces(b, eps, with_sumabs=True)
+    s = oracle.error_stats(acc.detach().cpu().numpy()[:, :3], ref_acc, sa)
+    assert s["rms_rel"] <= RMS_TOL and s["max_bound_ratio"] <= BOUND_K
+    ref_g = oracle.vjp(b, eps, W.cpu().numpy()[:, :3].astype(np.float64)) * (1.0 / cpd)   # d/d(offset in cells)
+    s = oracle.error_stats(pos.grad.cpu().numpy()[:, :3], ref_g)
+    assert s["rms_rel"] <= VJP_RMS_TOL, s
+
+
+# ------------------------------------------------------------------ batched, graphs, tuning
+
+def _boxes(k=6, seed=27):
+    rng = np.random.default_rng(seed)
+    specs = gen.batched_boxes(k, rng, n_lo=2000, n_hi=40000)
+    return specs, [make_box(s.pos, s.cpd, s.eps) for s in specs]
+
+
+def test_batched_equals_single_box_launches():
+    import paper_1810_02916_b300 as nfb
+    specs, boxes = _boxes()
+    single = [b.forces() for b in boxes]
+    batched = nfb.forces_batched(boxes)
+    for a, c in zip(single, batched):
+        assert np.array_equal(a, c)
+    for s, a in zip(specs[:2], batched[:2]):
+        ob = oracle_side(s.pos, s.cpd)
+        ref, sa, _ = oracle.forces(ob, s.eps, with_sumabs=True)
+        st = oracle.error_stats(a[:, :3], ref, sa)
+        assert st["rms_rel"] <= RMS_TOL and st["max_bound_ratio"] <= BOUND_K
+
+
+def test_batched_under_cuda_graph_replay():
+    torch = require_cuda()
+    import paper_1810_02916_b300 as nfb
+    _, boxes = _boxes(5, seed=28)
+    ref = [b.forces() for b in boxes]
+    s = torch.cuda.Stream()
+    for b in boxes:
+        b.set_stream(s)
+    outs = [torch.zeros((b.n, 4), device="cuda") for b in boxes]
+    with torch.cuda.stream(s):
+        nfb.forces_batched(boxes, outs)              # plans the batch (allocation happens here)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        nfb.forces_batched(boxes, outs)
+    for _ in range(2):
+        for o in outs:
+            o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            assert np.array_equal(o.cpu().numpy(), r)
+
+
+def test_tuner_picks_a_shape_and_keeps_results():
+    w = workload("clustered64")
+    nf = make_box(w.pos, w.cpd, w.eps)
+    a0 = nf.forces()
+    rep = nf.tune()
+    assert "->" in rep or rep == "cached"
+    a1 = nf.forces()
+    b = oracle_side(w.pos, w.cpd)
+    ref, sa, _ = oracle.forces(b, w.eps, with_sumabs=True)
+    for a in (a0, a1):
+        s = oracle.error_stats(a[:, :3], ref, sa)
+        assert s["rms_rel"] <= RMS_TOL and s["max_bound_ratio"] <= 2 * 256 + 64
+
+
+# ------------------------------------------------------------------ full sizes (sampled sinks)
+
+@pytest.mark.parametrize("name", ["clustered256", "zeldovich512"])
+def test_full_size_sampled_parity(name):
+    """The bench's workloads at full size, in the bench's launch shape, on sampled sinks."""
+    w = workload(name)
+    nf = make_box(w.pos, w.cpd, w.eps)
+    b = oracle_side(w.pos, w.cpd)
+    st = nf.get_particles()
+    assert np.array_equal(st["cell_offsets"], b.offsets)
+    assert np.array_equal(st["perm"], b.order)
+    assert np.array_equal(st["pos"][:, :3], b.xq)
+    del st
+    acc = nf.forces()
+    sinks = sample_sinks(b, 4000, seed=29)
+    ref, sa, _ = oracle.forces(b, w.eps, sinks, with_sumabs=True)
+    s = oracle.error_stats(acc[sinks, :3], ref, sa)
+    assert s["rms_rel"] <= RMS_TOL and s["max_bound_ratio"] <= BOUND_K, s
+    assert nf.pair_count() == oracle.pair_count(b)
