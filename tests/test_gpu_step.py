@@ -46,14 +46,14 @@ def test_one_kick_drift_step_matches_oracle():
     rng = np.random.default_rng(21)
     X, _ = gen.clustered(20000, rng, 4, 0.05, 0.2)
     w = 1.0 / cpd
-    dt = 1e-3
-    V = (rng.standard_normal((len(X), 3)) * 0.1 * w / dt).astype(np.float32)
     nf = make_box(X, cpd, eps)
     b = oracle_side(X, cpd)
+    nf.forces(False)
+    dt = float(np.sqrt(0.1 * eps / np.abs(nf.forces64()).max()))   # max |a| dt^2 = 0.1 eps
+    V = (rng.standard_normal((len(X), 3)) * 0.1 * w / dt).astype(np.float32)
     vel = np.zeros((nf.n, 4), np.float32)
     vel[:, :3] = V[b.order]
     nf.set_velocities(vel)
-    nf.forces(False)
     nf.kick_drift(dt)
     Xg, Vg = _global_by_id(nf.get_particles(), cpd)
     # oracle: FP64 forces on the same quantised start, FP64 kick and drift, re-binned
@@ -79,8 +79,9 @@ def test_ten_steps_track_the_oracle_trajectory():
     cpd, eps = 6, 0.3 / 6
     rng = np.random.default_rng(22)
     X = rng.random((6000, 3))
-    dt = 2e-4
     nf = make_box(X, cpd, eps)
+    nf.forces(False)
+    dt = float(np.sqrt(0.05 * eps / np.abs(nf.forces64()).max()))
     b = oracle_side(X, cpd)
     Xo = np.empty_like(X)
     Xo[b.order] = oracle.global_positions(b)
@@ -108,7 +109,8 @@ def test_kick_drift_keeps_canonical_order():
     vel[:, :3] = rng.standard_normal((nf.n, 3)).astype(np.float32) * 0.3
     nf.set_velocities(vel)
     nf.forces(False)
-    nf.kick_drift(0.05)
+    dt = min(0.05, float(np.sqrt(0.01 * (1.0 / cpd) / np.abs(nf.forces64()).max())))
+    nf.kick_drift(dt)
     st = nf.get_particles()
     Xg, _ = _global_by_id(st, cpd)
     nf2 = nfb.NearField(cpd, 1e-3)
