@@ -211,6 +211,36 @@ int nf_profile_read(nf_t *nf, int64_t *launches, double *ms);
 int nf_set_shape(nf_t *nf, int warps, int stage);
 int nf_tune(nf_t *nf, char *report, int report_len);
 
+/*
+ * nf_forces_noalloc -- nf_forces for callers that cannot allocate device
+ * memory (code living inside a memory pool it does not own, plugins whose
+ * host forbids new allocations after start-up, loops that must not pay for
+ * an allocation's implicit synchronisation).  The paper has no counterpart;
+ * it is the same pair kernel as nf_forces, driven without a box handle.
+ *   cpd, eps, box  as in nf_create (R = 2); 5 <= cpd <= 64
+ *   cell_start     device int32[cpd^3 + 1]: first particle of each cell, a
+ *                  non-decreasing scan from 0 to n
+ *   pos            device float[4 n], 16-byte aligned: cell-relative offsets
+ *                  in cell widths on the 2^-22 grid (as nf_get_particles
+ *                  returns them), sorted by cell
+ *   n              0 <= n <= 2^21
+ *   acc            device float[4 n], 16-byte aligned, out: accelerations in
+ *                  box units (compensated accumulation, as nf_forces)
+ *   stream         cudaStream_t for all work (NULL = legacy default stream)
+ *   err, err_len   optional buffer for a one-line message
+ * No cudaMalloc, cudaFree or other allocating call is made: the work list
+ * and counters live in one fixed device array of 6,555,392 bytes that every GPU
+ * loading the library holds until exit.  Its device address is looked up on
+ * the first call on each device, so make that first call before any stream
+ * capture.  Calls share that array and it keeps the last call's contents:
+ * calls whose GPU work overlaps (other streams, other threads) race and must
+ * be serialised by the caller.  The call synchronises `stream` once to
+ * validate cell_start.  NF_EINVAL for sizes beyond the limits above, host
+ * pointers, misaligned arrays or an invalid cell_start; NF_ECUDA otherwise.
+ */
+int nf_forces_noalloc(int cpd, double eps, double box, const int32_t *cell_start, const float *pos,
+                      int64_t n, float *acc, void *stream, char *err, int err_len);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

@@ -27,7 +27,7 @@ EXPORTS = [
     "nf_create", "nf_destroy", "nf_last_error", "nf_set_stream", "nf_set_accumulation", "nf_bin_particles",
     "nf_set_particles", "nf_set_velocities", "nf_get_particles", "nf_num_particles", "nf_pair_count", "nf_forces",
     "nf_get_forces64", "nf_kick_drift", "nf_vjp", "nf_forces_batched", "nf_profile", "nf_profile_read",
-    "nf_set_shape", "nf_tune",
+    "nf_set_shape", "nf_tune", "nf_forces_noalloc",
 ]
 
 
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
             "nf_profile_read": ([p, ctypes.POINTER(i64), ctypes.POINTER(d)], i),
             "nf_set_shape": ([p, i, i], i),
             "nf_tune": ([p, ctypes.c_char_p, i], i),
+            "nf_forces_noalloc": ([i, d, d, p, p, i64, p, p, ctypes.c_char_p, i], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
