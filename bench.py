@@ -318,6 +318,26 @@ def run(args):
     return 0
 
 
+def run_forces_only(args):
+    """Profiling driver: bin one workload, then `--forces-only` force passes (no bench line)."""
+    import torch
+    import paper_1810_02916_b300 as nfb
+    w = _make_workload(args.workload)
+    nf = nfb.NearField(w.cpd, w.eps, w.box)
+    if args.plain:
+        nf.set_accumulation(nfb.ACC_PLAIN)
+    nf.bin_particles(torch.from_numpy(w.pos).cuda())
+    acc = torch.empty((nf.n, 4), dtype=torch.float32, device="cuda")
+    nf.profile(True)
+    for _ in range(args.forces_only):
+        nf.forces(acc)
+    k, ms = nf.profile_read()
+    pairs = nf.pair_count()
+    print(json.dumps(dict(workload=args.workload, launches=k, ms_per_launch=ms / max(k, 1), pairs=pairs,
+                          gpair_s=pairs / (ms / max(k, 1) * 1e-3) / 1e9)), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,7 +349,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sinks", type=int, default=0, help="0: size the sample to --ref-seconds")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--workload", default=WORKLOAD, help="profiling driver only (with --forces-only)")
+    ap.add_argument("--forces-only", type=int, default=0, help="profiling driver: this many force passes")
+    ap.add_argument("--plain", action="store_true", help="profiling driver: plain FP32 accumulation")
     args = ap.parse_args()
+    if args.forces_only:
+        return run_forces_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run(args)
