@@ -181,7 +181,8 @@ void free_particles(nf_t *nf)
 
 int ensure_capacity(nf_t *nf, int64_t n)
 {
-    const int64_t item_cap = std::min<int64_t>(n, nf->ncell) + n / nf::kTile + 16;
+    // items per cell <= 1 + n_c / 16 (full tiles and remainder pieces of >= 16 sinks, plus one)
+    const int64_t item_cap = std::min<int64_t>(n, nf->ncell) + n / 16 + 16;
     if (n <= nf->cap && item_cap <= nf->item_cap && nf->pos) return NF_OK;
     cudaStreamSynchronize(nf->stream);
     free_particles(nf);

@@ -7,7 +7,7 @@
 // nf_forces_noalloc: it works on the caller's own device arrays (cell table,
 // positions, output) and keeps its work list and counters in one file-scope
 // device array of fixed size, g_scratch below.  Every GPU that loads the
-// library holds that array (6,555,392 bytes) until the process exits.
+// library holds that array (8,390,400 bytes) until the process exits.
 //
 // The host code reaches the array only through the device address returned
 // by cudaGetSymbolAddress: the symbol's name in host code is a host-side
@@ -25,7 +25,7 @@ namespace {
 constexpr int kMaxCpd = 64;
 constexpr int64_t kMaxCells = static_cast<int64_t>(kMaxCpd) * kMaxCpd * kMaxCpd;   // 262144
 constexpr int64_t kMaxParticles = int64_t(1) << 21;                              // 2097152
-constexpr int64_t kMaxItems = kMaxCells + kMaxParticles / nf::kTile + 16;
+constexpr int64_t kMaxItems = kMaxCells + kMaxParticles / 16 + 16;   // items per cell <= 1 + n_c / 16
 constexpr int kMaxDevices = 64;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -40,6 +40,8 @@ constexpr size_t kOffOffsets = align256(kOffCounts + sizeof(int) * kCellInts);
 constexpr size_t kOffScan = align256(kOffOffsets + sizeof(int) * kCellInts);
 constexpr size_t kOffWords = align256(kOffScan + sizeof(int) * kScanInts);   // n_items, queue, error flag
 constexpr size_t kScratchBytes = align256(kOffWords + 4 * sizeof(int));
+
+static_assert(kScratchBytes == 8390400, "the documented scratch size is out of date");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 

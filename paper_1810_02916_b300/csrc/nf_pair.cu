@@ -41,6 +41,10 @@
 namespace nf {
 namespace {
 
+#ifndef NF_MIN_BLOCKS
+#define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
+#endif
+
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kFar = 1.0e18f;   // padding source: y^3 underflows to 0, contributes exactly zero
 
@@ -95,8 +99,9 @@ __device__ __forceinline__ void pair_force(const float4 q, float xi, float yi, f
                                            float &az, float a0, float a1, float a2)
 {
     const float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
-    float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    r2 = fmaxf(r2, FLT_MIN);                 // r = 0 (self pair): finite g, times d = 0
+    // + FLT_MIN: below half an ulp of any nonzero r^2 on the 2^-22 grid (r^2 >= 2^-44), so it changes
+    // nothing except r = 0 (self pair), where it keeps rsqrt finite: finite g, times d = 0
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, FLT_MIN)));
     float y = rsqrtf(r2);                    // SFU
     const float t = r2 * y;
     const float h = t * y;
@@ -196,10 +201,10 @@ __device__ __forceinline__ int find_cell(const int *tpre, int f)
 
 // Gather sources [base, base + B) of the flattened neighbourhood into buf
 // (cp.async); entries past `total` become far-away padding.  The table slot
-// of each gathered entry is kept in tc[] for the shift pass.
+// of each gathered entry (plus one; 0 = padding) goes to ts[] for the shift pass.
 template <int B, bool ADJ>
 __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float4 *wbuf, const int *tstart,
-                                            const int *tpre, int base, int total, int lane, int (&tc)[B / 32])
+                                            const int *tpre, int base, int total, int lane, unsigned char *ts)
 {
 #pragma unroll
     for (int m = 0; m < B / 32; ++m) {
@@ -210,11 +215,11 @@ __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float
             const int src = tstart[t] + (f - tpre[t]);
             cp_async16(buf + slot, bx.pos + src);
             if (ADJ) cp_async16(wbuf + slot, bx.cot + src);
-            tc[m] = t;
+            ts[slot] = static_cast<unsigned char>(t + 1);
         } else {
             buf[slot] = make_float4(kFar, kFar, kFar, 0.f);
             if (ADJ) wbuf[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
-            tc[m] = -1;
+            ts[slot] = 0;
         }
     }
     cp_async_commit();
@@ -222,12 +227,13 @@ __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float
 
 // add the integer cell offset of each of this lane's landed entries
 template <int B>
-__device__ __forceinline__ void stage_shift(float4 *buf, int lane, const int (&tc)[B / 32])
+__device__ __forceinline__ void stage_shift(float4 *buf, int lane, const unsigned char *ts)
 {
 #pragma unroll
     for (int m = 0; m < B / 32; ++m) {
-        const int t = tc[m];
-        if (t >= 0) {
+        const int t1 = ts[m * 32 + lane];
+        if (t1) {
+            const int t = t1 - 1;
             float4 v = buf[m * 32 + lane];
             v.x += static_cast<float>(t / 25 - 2);
             v.y += static_cast<float>((t / 5) % 5 - 2);
@@ -237,10 +243,22 @@ __device__ __forceinline__ void stage_shift(float4 *buf, int lane, const int (&t
     }
 }
 
+// Compensated sums live in shared memory (per warp: 6 x 128 floats, slot =
+// sink slot of the lane), so the registers hold only positions and the
+// running FP32 partials of the current round.
+__device__ __forceinline__ void comp_fold_smem(float *c, float &px, float &py, float &pz)
+{
+    float s, e;
+    two_sum(c[0], px, s, e); c[0] = s; c[384] = __fadd_rn(c[384], e);
+    two_sum(c[128], py, s, e); c[128] = s; c[512] = __fadd_rn(c[512], e);
+    two_sum(c[256], pz, s, e); c[256] = s; c[640] = __fadd_rn(c[640], e);
+    px = py = pz = 0.f;
+}
+
 // S = 0: split mode (<= 16 sinks); S = 1, 2, 4: sinks per lane
 template <int S, int B, bool COMP, bool ADJ>
 __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, float4 *wstage, int *tstart, int *tpre,
-                         int lane)
+                         float *comp, unsigned char *tslot, int lane)
 {
     constexpr bool SPLIT = (S == 0);
     constexpr int SS = SPLIT ? 1 : S;
@@ -255,7 +273,6 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
 
     float xi[SS], yi[SS], zi[SS], wx[SS], wy[SS], wz[SS];
     float px[SS], py[SS], pz[SS];
-    Comp3 acc[SS];
 #pragma unroll
     for (int s = 0; s < SS; ++s) {
         const int k = SPLIT ? (lane & (P - 1)) : lane + 32 * s;
@@ -269,28 +286,29 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
             wx[s] = wy[s] = wz[s] = 0.f;
         }
         px[s] = py[s] = pz[s] = 0.f;
-        comp_init(acc[s]);
+        if (COMP) {
+            float *c = comp + lane + 32 * s;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) c[128 * q] = 0.f;
+        }
     }
     const float a0 = bx.a0, a1 = bx.a1, a2 = bx.a2, eps2 = bx.eps2;
 
     const int total = build_table(bx, item.cell, tstart, tpre, lane);
     const int rounds = (total + B - 1) / B;
 
-    int tc_cur[B / 32], tc_next[B / 32];
-#pragma unroll
-    for (int m = 0; m < B / 32; ++m) tc_next[m] = -1;
-    if (rounds > 0) stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, 0, total, lane, tc_cur);
+    if (rounds > 0) stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, 0, total, lane, tslot);
     for (int r = 0; r < rounds; ++r) {
         float4 *buf = stage + (r & 1) * B;
         float4 *wbuf = wstage + (r & 1) * B;
         if (r + 1 < rounds) {
             stage_issue<B, ADJ>(bx, stage + ((r + 1) & 1) * B, wstage + ((r + 1) & 1) * B, tstart, tpre, (r + 1) * B,
-                                total, lane, tc_next);
+                                total, lane, tslot + ((r + 1) & 1) * B);
             cp_async_wait_1();
         } else {
             cp_async_wait_0();
         }
-        stage_shift<B>(buf, lane, tc_cur);
+        stage_shift<B>(buf, lane, tslot + (r & 1) * B);
         __syncwarp();
         const int nr = min(B, total - r * B);
         if (SPLIT) {
@@ -323,16 +341,20 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
         }
         if (COMP) {
 #pragma unroll
-            for (int s = 0; s < SS; ++s) comp_fold(acc[s], px[s], py[s], pz[s]);
+            for (int s = 0; s < SS; ++s) comp_fold_smem(comp + lane + 32 * s, px[s], py[s], pz[s]);
         }
         __syncwarp();
-#pragma unroll
-        for (int m = 0; m < B / 32; ++m) tc_cur[m] = tc_next[m];
     }
-    if (!COMP) {
+    Comp3 acc[SS];
 #pragma unroll
-        for (int s = 0; s < SS; ++s) {
+    for (int s = 0; s < SS; ++s) {
+        if (COMP) {
+            const float *c = comp + lane + 32 * s;
+            acc[s].hx = c[0]; acc[s].hy = c[128]; acc[s].hz = c[256];
+            acc[s].lx = c[384]; acc[s].ly = c[512]; acc[s].lz = c[640];
+        } else {
             acc[s].hx = px[s]; acc[s].hy = py[s]; acc[s].hz = pz[s];
+            acc[s].lx = acc[s].ly = acc[s].lz = 0.f;
         }
     }
     if (SPLIT) {
@@ -366,17 +388,29 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
     }
 }
 
+// per-warp shared memory, in float4 units: staged sources (and cotangents),
+// compensated sums, neighbour table (256 ints), table slots (2 B bytes)
 template <int B, bool COMP, bool ADJ>
-__global__ void __launch_bounds__(256) pair_kernel(const BoxDev *__restrict__ boxes, const Item *__restrict__ items,
-                                                   const int *__restrict__ n_items_p, int *__restrict__ queue)
+__host__ __device__ constexpr int per_warp_f4()
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    constexpr int PER_WARP_F4 = (ADJ ? 4 : 2) * B;
-    float4 *stage = reinterpret_cast<float4 *>(smem_raw) + warp * PER_WARP_F4;
+    return (ADJ ? 4 : 2) * B + (COMP ? 192 : 0) + 64 + B / 8;
+}
+
+template <int B, bool COMP, bool ADJ>
+__global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *__restrict__ boxes,
+                                                                  const Item *__restrict__ items,
+                                                                  const int *__restrict__ n_items_p,
+                                                                  int *__restrict__ queue)
+{
+    extern __shared__ __align__(16) float4 smem_f4[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *w0 = smem_f4 + warp * per_warp_f4<B, COMP, ADJ>();
+    float4 *stage = w0;
     float4 *wstage = stage + 2 * B;
-    int *tabs = reinterpret_cast<int *>(reinterpret_cast<float4 *>(smem_raw) + nwarps * PER_WARP_F4) + warp * 256;
+    float *comp = reinterpret_cast<float *>(w0 + (ADJ ? 4 : 2) * B);
+    int *tabs = reinterpret_cast<int *>(w0 + (ADJ ? 4 : 2) * B + (COMP ? 192 : 0));
     int *tstart = tabs, *tpre = tabs + 128;
+    unsigned char *tslot = reinterpret_cast<unsigned char *>(tabs + 256);
     const int n_items = *n_items_p;
     for (;;) {
         int it = 0;
@@ -386,13 +420,13 @@ __global__ void __launch_bounds__(256) pair_kernel(const BoxDev *__restrict__ bo
         const Item item = items[it];
         const BoxDev &bx = boxes[item.box];
         if (item.sink_count <= 16)
-            run_item<0, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, lane);
+            run_item<0, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         else if (item.sink_count <= 32)
-            run_item<1, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, lane);
+            run_item<1, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         else if (item.sink_count <= 64)
-            run_item<2, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, lane);
+            run_item<2, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         else
-            run_item<4, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, lane);
+            run_item<4, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         __syncwarp();
     }
 }
@@ -400,7 +434,7 @@ __global__ void __launch_bounds__(256) pair_kernel(const BoxDev *__restrict__ bo
 template <int B, bool COMP, bool ADJ>
 size_t smem_bytes(int warps)
 {
-    return static_cast<size_t>(warps) * ((ADJ ? 4 : 2) * B * sizeof(float4) + 256 * sizeof(int));
+    return static_cast<size_t>(warps) * per_warp_f4<B, COMP, ADJ>() * sizeof(float4);
 }
 
 // Occupancy of one instantiation at `warps` warps per block, computed once

@@ -1,7 +1,12 @@
 // nf_plan.cu -- device-side work decomposition of the near-field pass.
 //
-// Every non-empty cell becomes ceil(n / 128) work items of up to 128 sinks
-// against the cell's whole 125-cell neighbourhood.  Items are written class
+// Every non-empty cell becomes work items of up to 128 sinks against the
+// cell's whole 125-cell neighbourhood: floor(n / 128) full tiles, and the
+// remainder r cut into pieces that fill the warp's lanes (64 sinks run with
+// 2 per lane, 32 with 1 per lane, <= 16 split the sources over the lanes):
+// r > 96 stays one tile; otherwise 64, 32 and 16 are taken while they fit
+// and the rest (<= 16) is the last piece.  A piece costs about its lanes x
+// neighbourhood, so this cuts the idle lanes of partly filled tiles.  Items are written class
 // by class of cell occupancy (>= 4096, >= 512, >= 64, >= 8, >= 1 particles),
 // so the persistent kernel takes the longest items first and the short ones
 // fill the tail (load imbalance across cells of very different density is
@@ -15,6 +20,28 @@ namespace {
 
 inline int nblocks(int64_t n, int per) { return static_cast<int>((n + per - 1) / per); }
 
+// sizes of the remainder pieces of r (0 < r < 128); returns how many (<= 4)
+__device__ __forceinline__ int remainder_pieces(int r, int *out)
+{
+    int k = 0;
+    if (r > 96) {
+        out[k++] = r;
+        return k;
+    }
+    if (r >= 64) { out[k++] = 64; r -= 64; }
+    if (r >= 32) { out[k++] = 32; r -= 32; }
+    if (r > 16) { out[k++] = 16; r -= 16; }
+    if (r > 0) out[k++] = r;
+    return k;
+}
+
+__device__ __forceinline__ int items_of_cell(int n)
+{
+    int tmp[4];
+    const int r = n % kTile;
+    return n / kTile + (r ? remainder_pieces(r, tmp) : 0);
+}
+
 __global__ void class_counts(const int *__restrict__ cell_start, int ncell, int cls, int *__restrict__ counts)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -24,7 +51,7 @@ __global__ void class_counts(const int *__restrict__ cell_start, int ncell, int 
         return;
     }
     const int n = cell_start[c + 1] - cell_start[c];
-    counts[c] = (n > 0 && occupancy_class(n) == cls) ? (n + kTile - 1) / kTile : 0;
+    counts[c] = (n > 0 && occupancy_class(n) == cls) ? items_of_cell(n) : 0;
 }
 
 __global__ void emit_items(const int *__restrict__ cell_start, int ncell, int cls, int box,
@@ -36,13 +63,25 @@ __global__ void emit_items(const int *__restrict__ cell_start, int ncell, int cl
     const int n = cell_start[c + 1] - s0;
     if (n <= 0 || occupancy_class(n) != cls) return;
     int out = *base_p + offsets[c];
-    for (int t = 0; t * kTile < n; ++t, ++out) {
-        Item it;
-        it.box = box;
-        it.cell = c;
-        it.sink_begin = s0 + t * kTile;
-        it.sink_count = min(kTile, n - t * kTile);
+    Item it;
+    it.box = box;
+    it.cell = c;
+    int begin = s0;
+    for (int t = 0; t < n / kTile; ++t, ++out, begin += kTile) {
+        it.sink_begin = begin;
+        it.sink_count = kTile;
         items[out] = it;
+    }
+    const int r = n % kTile;
+    if (r) {
+        int sz[4];
+        const int k = remainder_pieces(r, sz);
+        for (int q = 0; q < k; ++q, ++out) {
+            it.sink_begin = begin;
+            it.sink_count = sz[q];
+            items[out] = it;
+            begin += sz[q];
+        }
     }
 }
 
