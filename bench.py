@@ -338,6 +338,85 @@ def run_forces_only(args):
     return 0
 
 
+def run_batched(args):
+    """Secondary measurement: 64 independent boxes in one persistent launch replayed from a CUDA graph,
+    against one nf_forces launch per box on the same boxes."""
+    import torch
+    import paper_1810_02916_b300 as nfb
+    from synth import generators as gen
+    specs = gen.batched_boxes(64, gen.rng_for(3))
+    stream = torch.cuda.Stream()
+    boxes, outs = [], []
+    for sp in specs:
+        b = nfb.NearField(sp.cpd, sp.eps)
+        b.set_stream(stream)
+        b.bin_particles(torch.from_numpy(sp.pos).cuda())
+        boxes.append(b)
+        outs.append(torch.empty((b.n, 4), dtype=torch.float32, device="cuda"))
+    pairs = sum(b.pair_count() for b in boxes)
+    n = sum(b.n for b in boxes)
+    with torch.cuda.stream(stream):
+        nfb.forces_batched(boxes, outs)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        nfb.forces_batched(boxes, outs)
+    for _ in range(args.warmup):
+        g.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = e0.elapsed_time(e1) / args.steps
+    # one launch per box, same stream
+    for b, o in zip(boxes, outs):
+        b.forces(o)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for b, o in zip(boxes, outs):
+            b.forces(o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1) / args.steps
+    print(json.dumps(dict(mode="batched", boxes=len(boxes), particles=n, pairs=pairs,
+                          batched_graph=dict(ms=ms_graph, gpair_s=pairs / (ms_graph * 1e-3) / 1e9),
+                          one_launch_per_box=dict(ms=ms_single, gpair_s=pairs / (ms_single * 1e-3) / 1e9))),
+          flush=True)
+    return 0
+
+
+def run_adjoint(args):
+    """Secondary measurement: forward forces and the adjoint (VJP) kernel on the 64^3 clustered box."""
+    import torch
+    import paper_1810_02916_b300 as nfb
+    from synth import generators as gen
+    w = _make_workload("clustered64")
+    nf = nfb.NearField(w.cpd, w.eps, w.box)
+    nf.bin_particles(torch.from_numpy(w.pos).cuda())
+    W = torch.zeros((nf.n, 4), device="cuda")
+    W[:, :3] = torch.from_numpy(gen.cotangent(nf.n, gen.rng_for(5))).float().cuda()
+    acc = torch.empty_like(W)
+    grad = torch.empty_like(W)
+    pairs = nf.pair_count()
+    out = dict(mode="adjoint", workload="clustered64", particles=nf.n, pairs=pairs)
+    for name, fn in (("forces", lambda: nf.forces(acc)), ("vjp", lambda: nf.vjp(W, grad))):
+        for _ in range(args.warmup):
+            fn()
+        nf.profile(True)
+        for _ in range(args.steps):
+            fn()
+        k, ms = nf.profile_read()
+        nf.profile(False)
+        out[name] = dict(ms=ms / k, gpair_s=pairs / (ms / k * 1e-3) / 1e9)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,7 +431,13 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, help="profiling driver only (with --forces-only)")
     ap.add_argument("--forces-only", type=int, default=0, help="profiling driver: this many force passes")
     ap.add_argument("--plain", action="store_true", help="profiling driver: plain FP32 accumulation")
+    ap.add_argument("--mode", default="step", choices=["step", "batched", "adjoint"],
+                    help="batched / adjoint: secondary measurements (not the bench line)")
     args = ap.parse_args()
+    if args.mode == "batched":
+        return run_batched(args)
+    if args.mode == "adjoint":
+        return run_adjoint(args)
     if args.forces_only:
         return run_forces_only(args)
     if args.impl == "reference":

@@ -41,6 +41,9 @@
 namespace nf {
 namespace {
 
+#ifndef NF_SRC_UNROLL
+#define NF_SRC_UNROLL 8   // staged sources evaluated per unrolled step of the broadcast loop
+#endif
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
@@ -320,10 +323,11 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
                     pair_force(buf[j], xi[0], yi[0], zi[0], px[0], py[0], pz[0], a0, a1, a2);
             }
         } else {
-            const int nr4 = (nr + 3) & ~3;   // padding entries add exact zeros
-            for (int j = 0; j < nr4; j += 4) {
+            constexpr int U = NF_SRC_UNROLL;
+            const int nru = (nr + U - 1) / U * U;   // padding entries add exact zeros
+            for (int j = 0; j < nru; j += U) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < U; ++u) {
                     const float4 q = buf[j + u];
                     if (ADJ) {
                         const float4 wq = wbuf[j + u];
