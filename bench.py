@@ -162,17 +162,21 @@ def run_reference(args):
 
 
 def _launches_per_step(cpd):
-    """Kernels the library launches per step: forces (1) + kick-drift.
+    """Kernels the library launches per step (counted from the code; the ncu launch list agrees).
 
-    kick-drift: kick 1, drift 1, count 1, radix sort (hist, 3 scan kernels,
-    scatter per 8-bit pass), gather 1, cell-start scan 3, plan (1 reset +
-    5 classes x (counts, 3 scan kernels, emit, advance)).
+    forces: pair kernel + partial reduction = 2.
+    kick-drift: kick, drift, key count (3); radix sort, per 8-bit pass a histogram, three scan
+    kernels and a scatter (5 x passes); gather (1); cell-start scan (3); plan: counter reset (1),
+    5 occupancy classes x (count, three scan kernels, emit, advance) (30), neighbourhood sizes
+    (occupancy, three window sums, pair total: 5), source split (count, three scans of three
+    kernels, expand: 11).
     """
     ncell = cpd ** 3
     bits = max(1, (ncell - 1).bit_length())
     passes = (bits + 7) // 8
-    kick_drift = 1 + 1 + 1 + 5 * passes + 1 + 3 + (1 + 5 * 6)
-    return 1 + kick_drift
+    plan = 1 + 5 * 6 + 5 + 11
+    kick_drift = 3 + 5 * passes + 1 + 3 + plan
+    return 2 + kick_drift
 
 
 def run(args):

@@ -16,6 +16,8 @@
 using nf::BoxDev;
 using nf::Item;
 using nf::PairShape;
+using nf::Piece;
+using nf::Reduce;
 
 namespace {
 
@@ -55,9 +57,19 @@ struct nf_box {
     int *cell_start = nullptr, *counts = nullptr, *offsets = nullptr;
     void *scan_tmp = nullptr, *radix_tmp = nullptr;
     size_t radix_tmp_bytes = 0;
-    // plan
-    Item *items = nullptr;
-    int *n_items = nullptr, *queue = nullptr, *err = nullptr;
+    // plan: class-ordered items, then the same list with long items split into source pieces
+    Item *items_raw = nullptr, *items = nullptr;
+    int *n_raw = nullptr, *n_items = nullptr, *queue = nullptr, *err = nullptr;
+    Piece *pieces = nullptr;
+    Reduce *reduces = nullptr;
+    int *n_reduce = nullptr;
+    double *partials = nullptr;
+    int *split_k = nullptr, *split_p = nullptr, *split_r = nullptr;
+    void *split_scan = nullptr;
+    const int **nbr_ptr = nullptr;    // device copy of &offsets' current address (neighbourhood sizes)
+    const int *h_nbr = nullptr;
+    long long wf = 0;                 // resident warps (<= 32 per SM) x balance factor 4
+    int reduce_cap = 0;
     unsigned long long *pairs = nullptr;
     BoxDev *d_box = nullptr;
     BoxDev h_box{};                   // host mirror of *d_box
@@ -171,7 +183,10 @@ void free_particles(nf_t *nf)
     dfree(nf->pos); dfree(nf->vel); dfree(nf->acc64); dfree(nf->acc32); dfree(nf->cot);
     for (int k = 0; k < 2; ++k) { dfree(nf->keys[k]); dfree(nf->vals[k]); }
     dfree(nf->xq_by_id); dfree(nf->vel_by_id); dfree(nf->vel_tmp);
-    dfree(nf->items);
+    dfree(nf->items); dfree(nf->items_raw); dfree(nf->pieces); dfree(nf->reduces); dfree(nf->partials);
+    dfree(nf->split_k); dfree(nf->split_p); dfree(nf->split_r);
+    if (nf->split_scan) cudaFree(nf->split_scan);
+    nf->split_scan = nullptr;
     if (nf->radix_tmp) cudaFree(nf->radix_tmp);
     nf->radix_tmp = nullptr;
     nf->radix_tmp_bytes = 0;
@@ -196,10 +211,27 @@ int ensure_capacity(nf_t *nf, int64_t n)
         (rc = dalloc(nf, &nf->vals[0], u4)) || (rc = dalloc(nf, &nf->vals[1], u4)) ||
         (rc = dalloc(nf, &nf->xq_by_id, f4)) || (rc = dalloc(nf, &nf->vel_by_id, f4)) ||
         (rc = dalloc(nf, &nf->vel_tmp, f4)) ||
-        (rc = dalloc(nf, &nf->items, sizeof(Item) * static_cast<size_t>(item_cap)))) {
+        (rc = dalloc(nf, &nf->items_raw, sizeof(Item) * static_cast<size_t>(item_cap)))) {
         free_particles(nf);
         return rc;
     }
+    // splitting adds fewer than 2 wf items and reduce records, and at most 128 (2 wf) + n partial slots
+    const int64_t extra = 2 * nf->wf + 64;
+    const size_t split_items_cap = static_cast<size_t>(item_cap + extra);
+    const size_t slots = static_cast<size_t>(nf::kTile * extra + c);
+    const size_t scan_ints = static_cast<size_t>(item_cap) + 1;
+    if ((rc = dalloc(nf, &nf->items, sizeof(Item) * split_items_cap)) ||
+        (rc = dalloc(nf, &nf->pieces, sizeof(Piece) * split_items_cap)) ||
+        (rc = dalloc(nf, &nf->reduces, sizeof(Reduce) * static_cast<size_t>(extra))) ||
+        (rc = dalloc(nf, &nf->partials, 3 * sizeof(double) * slots)) ||
+        (rc = dalloc(nf, &nf->split_k, sizeof(int) * scan_ints)) ||
+        (rc = dalloc(nf, &nf->split_p, sizeof(int) * scan_ints)) ||
+        (rc = dalloc(nf, &nf->split_r, sizeof(int) * scan_ints)) ||
+        (rc = dalloc(nf, &nf->split_scan, nf::scan_temp_bytes(static_cast<int64_t>(scan_ints))))) {
+        free_particles(nf);
+        return rc;
+    }
+    nf->reduce_cap = static_cast<int>(extra);
     nf->radix_tmp_bytes = nf::radix_temp_bytes(c);
     if ((rc = dalloc(nf, &nf->radix_tmp, nf->radix_tmp_bytes))) {
         free_particles(nf);
@@ -210,6 +242,10 @@ int ensure_capacity(nf_t *nf, int64_t n)
     nf->box_dirty = true;
     return NF_OK;
 }
+
+// shortest source piece of a split item (the per-piece cost of the neighbour
+// table and the partial write stays below a few percent)
+constexpr int kSplitFloor = 1024;
 
 int key_bits(int ncell)
 {
@@ -226,6 +262,8 @@ void fill_box_desc(nf_t *nf, BoxDev &b, float4 *acc_out, double *acc64, const fl
     b.acc_out = acc_out;
     b.acc64 = acc64;
     b.cot = cot;
+    b.pieces = nf->pieces;
+    b.partials = nf->partials;
     b.cpd = nf->cpd;
     b.n = static_cast<int>(nf->n);
     b.a0 = static_cast<float>(10.0 / (ec * ec * ec));
@@ -251,10 +289,19 @@ int upload_box(nf_t *nf, float4 *acc_out, double *acc64, const float4 *cot)
 // items of this box (all classes, largest first) into nf->items
 int plan(nf_t *nf)
 {
-    NF_CK(nf::zero_device_int(nf->n_items, nf->stream));
+    NF_CK(nf::zero_device_int(nf->n_raw, nf->stream));
     for (int cls = 0; cls < nf::kClasses; ++cls)
-        NF_CK(nf::plan_items_class(nf->cell_start, nf->ncell, 0, cls, nf->items, nf->n_items, nf->counts,
+        NF_CK(nf::plan_items_class(nf->cell_start, nf->ncell, 0, cls, nf->items_raw, nf->n_raw, nf->counts,
                                    nf->offsets, nf->scan_tmp, nf->stream));
+    // neighbourhood sizes (left in offsets) and the pass's pair count, then the source split
+    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->pairs, nf->counts, nf->offsets, nf->stream));
+    if (nf->h_nbr != nf->offsets) {   // offsets and cell_start trade buffers in nf_set_particles
+        nf->h_nbr = nf->offsets;
+        NF_CK(cudaMemcpyAsync(nf->nbr_ptr, &nf->h_nbr, sizeof(int *), cudaMemcpyHostToDevice, nf->stream));
+    }
+    NF_CK(nf::split_items(nf->items_raw, nf->n_raw, static_cast<int>(nf->item_cap), nf->nbr_ptr, nf->pairs, nf->wf,
+                          kSplitFloor, nf->split_k, nf->split_p, nf->split_r, nf->split_scan, nf->items,
+                          nf->n_items, nf->pieces, nf->reduces, nf->n_reduce, nf->stream));
     return NF_OK;
 }
 
@@ -400,14 +447,18 @@ int nf_create(int cpd, int R, double eps, double box, nf_t **out)
         (rc = dalloc(nf, &nf->offsets, cells)) ||
         (rc = dalloc(nf, &nf->scan_tmp, nf::scan_temp_bytes(static_cast<int64_t>(nf->ncell) + 2))) ||
         (rc = dalloc(nf, &nf->n_items, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->queue, sizeof(int) * 4)) ||
+        (rc = dalloc(nf, &nf->n_raw, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->n_reduce, sizeof(int) * 4)) ||
+        (rc = dalloc(nf, &nf->nbr_ptr, sizeof(int *))) ||
         (rc = dalloc(nf, &nf->err, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->pairs, sizeof(unsigned long long))) ||
         (rc = dalloc(nf, &nf->d_box, sizeof(BoxDev)))) {
         g_create_error = nf->last_error;
         nf_destroy(nf);
         return rc;
     }
+    nf->wf = static_cast<long long>(nf->sm_count) * 32 * 4;
     e = cudaMemset(nf->cell_start, 0, cells);
     if (e == cudaSuccess) e = cudaMemset(nf->n_items, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(nf->n_reduce, 0, sizeof(int) * 4);
     if (e != cudaSuccess) {
         g_create_error = std::string("cudaMemset: ") + cudaGetErrorString(e);
         nf_destroy(nf);
@@ -429,6 +480,7 @@ void nf_destroy(nf_t *nf)
     dfree(nf->cell_start); dfree(nf->counts); dfree(nf->offsets);
     if (nf->scan_tmp) cudaFree(nf->scan_tmp);
     dfree(nf->n_items); dfree(nf->queue); dfree(nf->err); dfree(nf->pairs); dfree(nf->d_box);
+    dfree(nf->n_raw); dfree(nf->n_reduce); dfree(nf->nbr_ptr);
     if (nf->stage.p) cudaFree(nf->stage.p);
     for (cudaEvent_t e : nf->ev) cudaEventDestroy(e);
     delete nf;
@@ -627,7 +679,10 @@ int nf_forces(nf_t *nf, float *acc)
         }
     }
     if ((rc = upload_box(nf, out, nf->acc64, nullptr))) return rc;
-    if (nf->n > 0 && (rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
+    if (nf->n > 0) {
+        if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
+        NF_CK(nf::reduce_partials(nf->d_box, nf->reduces, nf->n_reduce, nf->reduce_cap, 0, nf->stream));
+    }
     if (copy_back) NF_CK(cudaMemcpyAsync(acc, nf->acc32, bytes, cudaMemcpyDefault, nf->stream));
     nf->have_forces = true;
     return NF_OK;
@@ -672,6 +727,7 @@ int nf_vjp(nf_t *nf, const float *w, float *grad)
     }
     if ((rc = upload_box(nf, out, nullptr, cot))) return rc;
     if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 1))) return rc;
+    NF_CK(nf::reduce_partials(nf->d_box, nf->reduces, nf->n_reduce, nf->reduce_cap, 1, nf->stream));
     if (copy_back) NF_CK(cudaMemcpyAsync(grad, nf->acc32, bytes, cudaMemcpyDefault, nf->stream));
     return NF_OK;
 }
@@ -808,14 +864,26 @@ int nf_tune(nf_t *nf, char *report, int report_len)
 
 namespace {
 
+// The combined plan of one set of boxes: class-major items over all boxes,
+// split into source pieces like a single box's plan, with its own partial
+// sums (every box descriptor of the batch points at them).
 struct Batch {
     std::vector<nf_t *> boxes;
     std::vector<uint64_t> gens;
     std::vector<BoxDev> h_desc;
     BoxDev *d_desc = nullptr;
-    Item *items = nullptr;
-    int64_t item_cap = 0;
-    int *n_items = nullptr, *queue = nullptr;
+    Item *items_raw = nullptr, *items = nullptr;
+    Piece *pieces = nullptr;
+    Reduce *reduces = nullptr;
+    double *partials = nullptr;
+    int *split_k = nullptr, *split_p = nullptr, *split_r = nullptr;
+    void *split_scan = nullptr;
+    const int **nbr_ptrs = nullptr;
+    const unsigned long long **pair_ptrs = nullptr;
+    unsigned long long *total = nullptr;
+    int64_t raw_cap = 0, n_cap = 0;
+    int nbox_cap = 0, reduce_cap = 0;
+    int *n_raw = nullptr, *n_items = nullptr, *n_reduce = nullptr, *queue = nullptr;
     int device = -1;
 };
 
@@ -839,11 +907,43 @@ namespace {
 
 void batch_release(Batch &b)
 {
-    if (b.d_desc) cudaFree(b.d_desc);
-    if (b.items) cudaFree(b.items);
-    if (b.n_items) cudaFree(b.n_items);
-    if (b.queue) cudaFree(b.queue);
+    void *ps[] = {b.d_desc, b.items_raw, b.items, b.pieces, b.reduces, b.partials, b.split_k, b.split_p,
+                  b.split_r, b.split_scan, b.nbr_ptrs, b.pair_ptrs, b.total, b.n_raw, b.n_items, b.n_reduce, b.queue};
+    for (void *q : ps)
+        if (q) cudaFree(q);
     b = Batch();
+}
+
+int batch_alloc(nf_t *nf, Batch &B, int nbox, int64_t raw_cap, int64_t n_total)
+{
+    batch_release(B);
+    const int64_t extra = 2 * nf->wf + 64;
+    const size_t items_cap = static_cast<size_t>(raw_cap + extra);
+    const size_t scan_ints = static_cast<size_t>(raw_cap) + 1;
+    const size_t slots = static_cast<size_t>(nf::kTile * extra + n_total);
+    int rc;
+    if ((rc = dalloc(nf, &B.d_desc, sizeof(BoxDev) * nbox)) ||
+        (rc = dalloc(nf, &B.items_raw, sizeof(Item) * static_cast<size_t>(raw_cap))) ||
+        (rc = dalloc(nf, &B.items, sizeof(Item) * items_cap)) || (rc = dalloc(nf, &B.pieces, sizeof(Piece) * items_cap)) ||
+        (rc = dalloc(nf, &B.reduces, sizeof(Reduce) * static_cast<size_t>(extra))) ||
+        (rc = dalloc(nf, &B.partials, 3 * sizeof(double) * slots)) ||
+        (rc = dalloc(nf, &B.split_k, sizeof(int) * scan_ints)) || (rc = dalloc(nf, &B.split_p, sizeof(int) * scan_ints)) ||
+        (rc = dalloc(nf, &B.split_r, sizeof(int) * scan_ints)) ||
+        (rc = dalloc(nf, &B.split_scan, nf::scan_temp_bytes(static_cast<int64_t>(scan_ints)))) ||
+        (rc = dalloc(nf, &B.nbr_ptrs, sizeof(int *) * nbox)) ||
+        (rc = dalloc(nf, &B.pair_ptrs, sizeof(unsigned long long *) * nbox)) ||
+        (rc = dalloc(nf, &B.total, sizeof(unsigned long long))) || (rc = dalloc(nf, &B.n_raw, sizeof(int) * 4)) ||
+        (rc = dalloc(nf, &B.n_items, sizeof(int) * 4)) || (rc = dalloc(nf, &B.n_reduce, sizeof(int) * 4)) ||
+        (rc = dalloc(nf, &B.queue, sizeof(int) * 4))) {
+        batch_release(B);
+        return rc;
+    }
+    B.raw_cap = raw_cap;
+    B.n_cap = n_total;
+    B.nbox_cap = nbox;
+    B.reduce_cap = static_cast<int>(extra);
+    B.device = nf->device;
+    return NF_OK;
 }
 
 }  // namespace
@@ -864,32 +964,40 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
     bool same = B.device == nf->device && static_cast<int>(B.boxes.size()) == nbox;
     for (int b = 0; same && b < nbox; ++b) same = B.boxes[b] == boxes[b] && B.gens[b] == boxes[b]->generation;
     if (!same) {
-        // (re)plan: one item list over all boxes, class-major (largest cells first)
+        // (re)plan: one item list over all boxes, class-major (largest cells first), then split
         cudaStreamSynchronize(nf->stream);
-        int64_t need = 16;
-        for (int b = 0; b < nbox; ++b) need += boxes[b]->item_cap;
-        if (B.device != nf->device || need > B.item_cap || static_cast<int>(B.h_desc.size()) < nbox) {
-            batch_release(B);
-            if ((rc = dalloc(nf, &B.items, sizeof(Item) * static_cast<size_t>(need))) ||
-                (rc = dalloc(nf, &B.d_desc, sizeof(BoxDev) * static_cast<size_t>(nbox))) ||
-                (rc = dalloc(nf, &B.n_items, sizeof(int) * 4)) || (rc = dalloc(nf, &B.queue, sizeof(int) * 4))) {
-                batch_release(B);
-                return rc;
-            }
-            B.item_cap = need;
-            B.device = nf->device;
-            B.h_desc.assign(nbox, BoxDev{});
+        int64_t raw_cap = 16, n_total = 0;
+        for (int b = 0; b < nbox; ++b) {
+            raw_cap += boxes[b]->item_cap;
+            n_total += boxes[b]->n;
         }
-        NF_CK(nf::zero_device_int(B.n_items, nf->stream));
+        if (B.device != nf->device || raw_cap > B.raw_cap || n_total > B.n_cap || nbox > B.nbox_cap) {
+            if ((rc = batch_alloc(nf, B, nbox, raw_cap, n_total))) return rc;
+        }
+        NF_CK(nf::zero_device_int(B.n_raw, nf->stream));
         for (int cls = 0; cls < nf::kClasses; ++cls)
             for (int b = 0; b < nbox; ++b)
-                NF_CK(nf::plan_items_class(boxes[b]->cell_start, boxes[b]->ncell, b, cls, B.items, B.n_items,
+                NF_CK(nf::plan_items_class(boxes[b]->cell_start, boxes[b]->ncell, b, cls, B.items_raw, B.n_raw,
                                            boxes[b]->counts, boxes[b]->offsets, boxes[b]->scan_tmp, nf->stream));
+        std::vector<const int *> nbr(nbox);
+        std::vector<const unsigned long long *> prs(nbox);
+        for (int b = 0; b < nbox; ++b) {
+            nf_t *x = boxes[b];
+            NF_CK(nf::neighbour_pairs(x->cell_start, x->cpd, x->pairs, x->counts, x->offsets, nf->stream));
+            nbr[b] = x->offsets;
+            prs[b] = x->pairs;
+        }
+        NF_CK(cudaMemcpyAsync(B.nbr_ptrs, nbr.data(), sizeof(int *) * nbox, cudaMemcpyHostToDevice, nf->stream));
+        NF_CK(cudaMemcpyAsync(B.pair_ptrs, prs.data(), sizeof(void *) * nbox, cudaMemcpyHostToDevice, nf->stream));
+        NF_CK(nf::sum_pair_counts(B.pair_ptrs, nbox, B.total, nf->stream));
+        NF_CK(nf::split_items(B.items_raw, B.n_raw, static_cast<int>(B.raw_cap), B.nbr_ptrs, B.total, nf->wf,
+                              kSplitFloor, B.split_k, B.split_p, B.split_r, B.split_scan, B.items, B.n_items, B.pieces,
+                              B.reduces, B.n_reduce, nf->stream));
+        NF_CK(cudaStreamSynchronize(nf->stream));   // the host vectors above must outlive their copies
         B.boxes.assign(boxes, boxes + nbox);
         B.gens.resize(nbox);
         for (int b = 0; b < nbox; ++b) B.gens[b] = boxes[b]->generation;
-        std::fill(B.h_desc.begin(), B.h_desc.end(), BoxDev{});
-        B.h_desc.resize(nbox);
+        B.h_desc.assign(nbox, BoxDev{});
         NF_CK(cudaMemsetAsync(B.d_desc, 0, sizeof(BoxDev) * nbox, nf->stream));
     }
     // descriptors (uploaded only when an output pointer changed)
@@ -910,6 +1018,8 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
         }
         BoxDev d{};
         fill_box_desc(x, d, out, x->acc64, nullptr);
+        d.pieces = B.pieces;
+        d.partials = B.partials;
         if (std::memcmp(&d, &B.h_desc[b], sizeof(BoxDev)) != 0) {
             B.h_desc[b] = d;
             dirty = true;
@@ -918,6 +1028,7 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
     if (dirty)
         NF_CK(cudaMemcpyAsync(B.d_desc, B.h_desc.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice, nf->stream));
     if ((rc = launch_forces(nf, B.d_desc, B.items, B.n_items, B.queue, 0))) return rc;
+    NF_CK(nf::reduce_partials(B.d_desc, B.reduces, B.n_reduce, B.reduce_cap, 0, nf->stream));
     for (int b = 0; b < nbox; ++b) {
         boxes[b]->have_forces = true;
         if (copy_back[b])

@@ -12,6 +12,16 @@ constexpr int kR = 2;
 constexpr int kNbr = (2 * kR + 1) * (2 * kR + 1) * (2 * kR + 1);   // 125
 constexpr int kTile = 128;                                            // sinks per work item (max)
 
+// A source range of one work item whose sink tile is split over several
+// warps: flattened neighbourhood sources [src_lo, src_hi), FP64 partial sums
+// written at partials[3 * (slot + k)] for the item's k-th sink.
+struct Piece {
+    int src_lo;
+    int src_hi;
+    int slot;
+    int pad;
+};
+
 // One box as the kernels see it.
 struct BoxDev {
     const float4 *pos;        // n, cell-relative offsets (cell widths), sorted by cell
@@ -19,6 +29,8 @@ struct BoxDev {
     float4 *acc_out;          // n, FP32 output in box units (may be null)
     double *acc64;            // 3 n, FP64 output in box units (may be null)
     const float4 *cot;        // n, cotangent for the adjoint (null for forces)
+    const Piece *pieces;      // source ranges of split items (null when nothing is split)
+    double *partials;         // FP64 partial sums of split items, cell units
     int cpd;
     int n;
     float a0, a1, a2;         // spline g(r) = a0 + a1 r + a2 r^2 in cell units
@@ -27,12 +39,23 @@ struct BoxDev {
     double grad_scale;        // (cpd / box)^3: cell-unit Jacobian -> box units
 };
 
-// A work item: up to kTile sinks of one cell against its whole neighbourhood.
+// A work item: up to kTile sinks of one cell against its neighbourhood (or a
+// piece of it).  box and sink count share one word: (box << 16) | count.
 struct Item {
-    int box;
+    int box_count;
     int cell;
     int sink_begin;
-    int sink_count;
+    int piece;                // -1: the whole neighbourhood, final output; else index into pieces
+};
+__host__ __device__ inline int item_box(const Item &it) { return it.box_count >> 16; }
+__host__ __device__ inline int item_count(const Item &it) { return it.box_count & 0xffff; }
+
+// Sinks of a split item whose partials are summed (in piece order) by reduce_partials.
+struct Reduce {
+    int box_count;
+    int sink_begin;
+    int slot;
+    int pieces;
 };
 
 // Occupancy classes used to order the work queue (largest cells first).
@@ -76,6 +99,19 @@ cudaError_t count_keys(const uint32_t *keys, int n, int *counts, cudaStream_t st
 cudaError_t plan_items_class(const int *cell_start, int ncell, int box_index, int cls, Item *items, int *n_items,
                              int *scratch_counts, int *scratch_offsets, void *scan_temp, cudaStream_t st);
 cudaError_t zero_device_int(int *p, cudaStream_t st);
+// Split items whose neighbourhood is long against the whole pass into source
+// pieces (see nf_plan.cu).  items_in/n_in: the class-ordered list; nbr[box]:
+// sources in each cell's neighbourhood of that box; total_pairs: pair count of the pass; warps_x_f:
+// resident warps times the balance factor.  Scratch k/p/r: item_cap + 1 ints
+// each.  Writes items_out/n_out, pieces, reduces/n_reduce.
+cudaError_t split_items(const Item *items_in, const int *n_in, int item_cap, const int *const *nbr,
+                        const unsigned long long *total_pairs, long long warps_x_f, int t_floor, int *k, int *p,
+                        int *r, void *scan_temp, Item *items_out, int *n_out, Piece *pieces, Reduce *reduces,
+                        int *n_reduce, cudaStream_t st);
+// *out = sum of the n values at ptrs[0..n)
+cudaError_t sum_pair_counts(const unsigned long long *const *ptrs, int n, unsigned long long *out, cudaStream_t st);
+cudaError_t reduce_partials(const BoxDev *boxes, const Reduce *reduces, const int *n_reduce, int max_reduce,
+                            int adjoint, cudaStream_t st);
 cudaError_t neighbour_pairs(const int *cell_start, int cpd, unsigned long long *pairs, int *tmp_a, int *tmp_b,
                             cudaStream_t st);
 

@@ -265,7 +265,7 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
 {
     constexpr bool SPLIT = (S == 0);
     constexpr int SS = SPLIT ? 1 : S;
-    const int count = item.sink_count;
+    const int count = item_count(item);
     int logp = 0;
     if (SPLIT) {
         while ((1 << logp) < count) ++logp;
@@ -298,22 +298,30 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
     const float a0 = bx.a0, a1 = bx.a1, a2 = bx.a2, eps2 = bx.eps2;
 
     const int total = build_table(bx, item.cell, tstart, tpre, lane);
-    const int rounds = (total + B - 1) / B;
+    // the whole flattened neighbourhood, or this item's piece of it
+    int src_lo = 0, src_hi = total, slot = -1;
+    if (item.piece >= 0) {
+        const Piece pc = bx.pieces[item.piece];
+        src_lo = pc.src_lo;
+        src_hi = min(pc.src_hi, total);
+        slot = pc.slot;
+    }
+    const int rounds = src_hi > src_lo ? (src_hi - src_lo + B - 1) / B : 0;
 
-    if (rounds > 0) stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, 0, total, lane, tslot);
+    if (rounds > 0) stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, src_lo, src_hi, lane, tslot);
     for (int r = 0; r < rounds; ++r) {
         float4 *buf = stage + (r & 1) * B;
         float4 *wbuf = wstage + (r & 1) * B;
         if (r + 1 < rounds) {
-            stage_issue<B, ADJ>(bx, stage + ((r + 1) & 1) * B, wstage + ((r + 1) & 1) * B, tstart, tpre, (r + 1) * B,
-                                total, lane, tslot + ((r + 1) & 1) * B);
+            stage_issue<B, ADJ>(bx, stage + ((r + 1) & 1) * B, wstage + ((r + 1) & 1) * B, tstart, tpre,
+                                src_lo + (r + 1) * B, src_hi, lane, tslot + ((r + 1) & 1) * B);
             cp_async_wait_1();
         } else {
             cp_async_wait_0();
         }
         stage_shift<B>(buf, lane, tslot + (r & 1) * B);
         __syncwarp();
-        const int nr = min(B, total - r * B);
+        const int nr = min(B, src_hi - src_lo - r * B);
         if (SPLIT) {
             for (int j = my_split; j < nr; j += splits) {
                 if (ADJ)
@@ -372,6 +380,20 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
             }
         }
     }
+    if (slot >= 0) {
+        // a piece of a split item: FP64 partial sums (cell units), reduced later in piece order
+#pragma unroll
+        for (int s = 0; s < SS; ++s) {
+            const int k = SPLIT ? lane : lane + 32 * s;
+            if (k < count) {
+                double *o = bx.partials + 3 * (static_cast<int64_t>(slot) + k);
+                o[0] = static_cast<double>(acc[s].hx) + static_cast<double>(acc[s].lx);
+                o[1] = static_cast<double>(acc[s].hy) + static_cast<double>(acc[s].ly);
+                o[2] = static_cast<double>(acc[s].hz) + static_cast<double>(acc[s].lz);
+            }
+        }
+        return;
+    }
     const double scale = ADJ ? bx.grad_scale : bx.acc_scale;
 #pragma unroll
     for (int s = 0; s < SS; ++s) {
@@ -422,12 +444,13 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
         it = __shfl_sync(kFull, it, 0);
         if (it >= n_items) break;
         const Item item = items[it];
-        const BoxDev &bx = boxes[item.box];
-        if (item.sink_count <= 16)
+        const BoxDev &bx = boxes[item_box(item)];
+        const int cnt = item_count(item);
+        if (cnt <= 16)
             run_item<0, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
-        else if (item.sink_count <= 32)
+        else if (cnt <= 32)
             run_item<1, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
-        else if (item.sink_count <= 64)
+        else if (cnt <= 64)
             run_item<2, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         else
             run_item<4, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);

@@ -64,12 +64,12 @@ __global__ void emit_items(const int *__restrict__ cell_start, int ncell, int cl
     if (n <= 0 || occupancy_class(n) != cls) return;
     int out = *base_p + offsets[c];
     Item it;
-    it.box = box;
     it.cell = c;
+    it.piece = -1;
     int begin = s0;
     for (int t = 0; t < n / kTile; ++t, ++out, begin += kTile) {
         it.sink_begin = begin;
-        it.sink_count = kTile;
+        it.box_count = (box << 16) | kTile;
         items[out] = it;
     }
     const int r = n % kTile;
@@ -78,7 +78,7 @@ __global__ void emit_items(const int *__restrict__ cell_start, int ncell, int cl
         const int k = remainder_pieces(r, sz);
         for (int q = 0; q < k; ++q, ++out) {
             it.sink_begin = begin;
-            it.sink_count = sz[q];
+            it.box_count = (box << 16) | sz[q];
             items[out] = it;
             begin += sz[q];
         }
@@ -129,7 +129,161 @@ __global__ void dot_counts(const int *__restrict__ cell_start, const int *__rest
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
 }
 
+// ---- source splitting of long items (deterministic: fixed pieces, fixed reduction order)
+//
+// An item of s sinks whose neighbourhood holds T sources costs s T pairs.  A
+// pass of P pairs on W resident warps balances when no item is much longer
+// than P / (W F); items with T above T_max(s) = max(t_floor, P / (W F s)) are
+// cut into k = ceil(T / T_max) (<= 64) contiguous ranges of the flattened
+// neighbourhood.  Each piece writes FP64 partial sums; reduce_partials adds
+// them per sink in piece order.  (Sum over split items of (k - 1) <= W F, so
+// the extra items and partial slots are bounded by the launch size.)
+
+__global__ void split_count(const Item *__restrict__ items, const int *__restrict__ n_in, int cap,
+                            const int *const *__restrict__ nbr, const unsigned long long *__restrict__ total_pairs,
+                            long long warps_x_f, int t_floor, int *__restrict__ k, int *__restrict__ p,
+                            int *__restrict__ r)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > cap) return;
+    int kk = 0, pp = 0, rr = 0;
+    if (i < *n_in) {
+        const Item it = items[i];
+        const long long s = item_count(it);
+        const long long T = nbr[item_box(it)][it.cell];
+        long long target = static_cast<long long>(*total_pairs) / (warps_x_f > 0 ? warps_x_f : 1);
+        long long tmax = target / (s > 0 ? s : 1);
+        if (tmax < t_floor) tmax = t_floor;
+        kk = 1;
+        if (T > tmax) {
+            long long q = (T + tmax - 1) / tmax;
+            kk = static_cast<int>(q > 64 ? 64 : q);
+            pp = kk * static_cast<int>(s);
+            rr = 1;
+        }
+    }
+    k[i] = kk;
+    p[i] = pp;
+    r[i] = rr;
+}
+
+// k, p, r hold exclusive scans here; counts are recovered from neighbours
+__global__ void split_expand(const Item *__restrict__ items, const int *__restrict__ n_in,
+                             const int *const *__restrict__ nbr, const int *__restrict__ k, const int *__restrict__ p,
+                             const int *__restrict__ r, Item *__restrict__ out, int *__restrict__ n_out,
+                             Piece *__restrict__ pieces, Reduce *__restrict__ reduces, int *__restrict__ n_reduce)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = *n_in;
+    if (i == 0) {
+        *n_out = k[n];
+        *n_reduce = r[n];
+    }
+    if (i >= n) return;
+    const Item it = items[i];
+    const int base = k[i];
+    const int kk = k[i + 1] - base;
+    if (kk == 1) {
+        out[base] = it;
+        return;
+    }
+    const int s = item_count(it);
+    const int T = nbr[item_box(it)][it.cell];
+    for (int j = 0; j < kk; ++j) {
+        Item o = it;
+        o.piece = base + j;
+        out[base + j] = o;
+        Piece pc;
+        pc.src_lo = static_cast<int>(static_cast<long long>(T) * j / kk);
+        pc.src_hi = static_cast<int>(static_cast<long long>(T) * (j + 1) / kk);
+        pc.slot = p[i] + j * s;
+        pc.pad = 0;
+        pieces[base + j] = pc;
+    }
+    Reduce rd;
+    rd.box_count = it.box_count;
+    rd.sink_begin = it.sink_begin;
+    rd.slot = p[i];
+    rd.pieces = kk;
+    reduces[r[i]] = rd;
+}
+
+// one thread per (reduce record, sink slot); partials summed in piece order
+__global__ void reduce_kernel(const BoxDev *__restrict__ boxes, const Reduce *__restrict__ reduces,
+                              const int *__restrict__ n_reduce, int adjoint)
+{
+    const int rec = blockIdx.x;
+    if (rec >= *n_reduce) return;
+    const Reduce rd = reduces[rec];
+    const int s = rd.box_count & 0xffff;
+    const int k = threadIdx.x;
+    if (k >= s) return;
+    const BoxDev &bx = boxes[rd.box_count >> 16];
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < rd.pieces; ++j) {
+        const double *q = bx.partials + 3 * (static_cast<int64_t>(rd.slot) + static_cast<int64_t>(j) * s + k);
+        a[0] += q[0];
+        a[1] += q[1];
+        a[2] += q[2];
+    }
+    const double scale = adjoint ? bx.grad_scale : bx.acc_scale;
+    const int idx = rd.sink_begin + k;
+    const double gx = a[0] * scale, gy = a[1] * scale, gz = a[2] * scale;
+    if (bx.acc64) {
+        double *o = bx.acc64 + 3 * static_cast<int64_t>(idx);
+        o[0] = gx; o[1] = gy; o[2] = gz;
+    }
+    if (bx.acc_out)
+        bx.acc_out[idx] = make_float4(static_cast<float>(gx), static_cast<float>(gy), static_cast<float>(gz), 0.f);
+}
+
 }  // namespace
+
+__global__ void sum_kernel(const unsigned long long *const *ptrs, int n, unsigned long long *out)
+{
+    unsigned long long s = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += *ptrs[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ unsigned long long w[32];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) t += w[i];
+        *out = t;
+    }
+}
+
+cudaError_t sum_pair_counts(const unsigned long long *const *ptrs, int n, unsigned long long *out, cudaStream_t st)
+{
+    sum_kernel<<<1, 256, 0, st>>>(ptrs, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t split_items(const Item *items_in, const int *n_in, int item_cap, const int *const *nbr,
+                        const unsigned long long *total_pairs, long long warps_x_f, int t_floor, int *k, int *p,
+                        int *r, void *scan_temp, Item *items_out, int *n_out, Piece *pieces, Reduce *reduces,
+                        int *n_reduce, cudaStream_t st)
+{
+    const int64_t m = static_cast<int64_t>(item_cap) + 1;
+    split_count<<<nblocks(m, 256), 256, 0, st>>>(items_in, n_in, item_cap, nbr, total_pairs, warps_x_f, t_floor, k, p,
+                                                 r);
+    cudaError_t e;
+    if ((e = exclusive_scan_i32(k, k, m, scan_temp, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan_i32(p, p, m, scan_temp, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan_i32(r, r, m, scan_temp, st)) != cudaSuccess) return e;
+    split_expand<<<nblocks(m, 256), 256, 0, st>>>(items_in, n_in, nbr, k, p, r, items_out, n_out, pieces, reduces,
+                                                  n_reduce);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_partials(const BoxDev *boxes, const Reduce *reduces, const int *n_reduce, int max_reduce,
+                            int adjoint, cudaStream_t st)
+{
+    if (max_reduce <= 0) return cudaSuccess;
+    reduce_kernel<<<max_reduce, kTile, 0, st>>>(boxes, reduces, n_reduce, adjoint);
+    return cudaGetLastError();
+}
 
 cudaError_t zero_device_int(int *p, cudaStream_t st)
 {

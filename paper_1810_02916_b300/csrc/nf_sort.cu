@@ -86,8 +86,8 @@ __global__ void scan_partials(int *__restrict__ partials, int nb)
     }
 }
 
-__global__ void scan_down(const int *__restrict__ in, int *__restrict__ out, int64_t n,
-                          const int *__restrict__ partials)
+// in == out is allowed: every thread reads its own items before any write
+__global__ void scan_down(const int *in, int *out, int64_t n, const int *__restrict__ partials)
 {
     __shared__ int ws[33];
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + threadIdx.x * kScanItems;
