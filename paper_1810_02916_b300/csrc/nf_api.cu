@@ -245,7 +245,10 @@ int ensure_capacity(nf_t *nf, int64_t n)
 
 // shortest source piece of a split item (the per-piece cost of the neighbour
 // table and the partial write stays below a few percent)
-constexpr int kSplitFloor = 1024;
+#ifndef NF_SPLIT_FLOOR
+#define NF_SPLIT_FLOOR 1024
+#endif
+constexpr int kSplitFloor = NF_SPLIT_FLOOR;
 
 int key_bits(int ncell)
 {

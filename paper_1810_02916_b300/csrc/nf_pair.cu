@@ -299,12 +299,10 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
 
     const int total = build_table(bx, item.cell, tstart, tpre, lane);
     // the whole flattened neighbourhood, or this item's piece of it
-    int src_lo = 0, src_hi = total, slot = -1;
+    int src_lo = 0, src_hi = total;
     if (item.piece >= 0) {
-        const Piece pc = bx.pieces[item.piece];
-        src_lo = pc.src_lo;
-        src_hi = min(pc.src_hi, total);
-        slot = pc.slot;
+        src_lo = __ldg(&bx.pieces[item.piece].src_lo);
+        src_hi = min(__ldg(&bx.pieces[item.piece].src_hi), total);
     }
     const int rounds = src_hi > src_lo ? (src_hi - src_lo + B - 1) / B : 0;
 
@@ -380,8 +378,9 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
             }
         }
     }
-    if (slot >= 0) {
+    if (item.piece >= 0) {
         // a piece of a split item: FP64 partial sums (cell units), reduced later in piece order
+        const int slot = __ldg(&bx.pieces[item.piece].slot);
 #pragma unroll
         for (int s = 0; s < SS; ++s) {
             const int k = SPLIT ? lane : lane + 32 * s;

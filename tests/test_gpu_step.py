@@ -168,13 +168,18 @@ def _boxes(k=6, seed=27):
     return specs, [make_box(s.pos, s.cpd, s.eps) for s in specs]
 
 
-def test_batched_equals_single_box_launches():
+def test_batched_matches_single_box_launches():
+    """One launch over all boxes gives each box's forces; the batch splits long items against the
+    whole batch's work, so sums may be grouped differently than in a single-box launch (rounding only)."""
     import paper_1810_02916_b300 as nfb
     specs, boxes = _boxes()
     single = [b.forces() for b in boxes]
     batched = nfb.forces_batched(boxes)
-    for a, c in zip(single, batched):
-        assert np.array_equal(a, c)
+    again = nfb.forces_batched(boxes)
+    for a, c, d in zip(single, batched, again):
+        assert np.array_equal(c, d)                     # deterministic
+        s = oracle.error_stats(c[:, :3], a[:, :3].astype(np.float64))
+        assert s["rms_rel"] <= RMS_TOL, s              # both sides are within RMS_TOL of the oracle
     for s, a in zip(specs[:2], batched[:2]):
         ob = oracle_side(s.pos, s.cpd)
         ref, sa, _ = oracle.forces(ob, s.eps, with_sumabs=True)
@@ -186,7 +191,7 @@ def test_batched_under_cuda_graph_replay():
     torch = require_cuda()
     import paper_1810_02916_b300 as nfb
     _, boxes = _boxes(5, seed=28)
-    ref = [b.forces() for b in boxes]
+    ref = nfb.forces_batched(boxes)                 # the same plan, launched without a graph
     s = torch.cuda.Stream()
     for b in boxes:
         b.set_stream(s)
