@@ -161,6 +161,20 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(x: float, device: str = "cpu") -> float:
+    """Largest value of x over all ranks of the default process group (timing only)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(pairs_per_replica: int, world: int, step_ms: float) -> float:
+    """Gpair/s of the whole job: every rank evaluates its own replica in step_ms (the slowest rank's time)."""
+    return world * pairs_per_replica / (step_ms * 1e-3) / 1e9
+
+
 def _launches_per_step(cpd):
     """Kernels the library launches per step (counted from the code; the ncu launch list agrees).
 
@@ -234,12 +248,8 @@ def run(args):
     clk = clocks.stop()
     launches, pair_ms = nf.profile_read()
     pair_ms /= max(launches, 1)
-    t_max = step_ms
-    if world > 1:
-        t = torch.tensor([step_ms], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * pairs / (t_max * 1e-3) / 1e9
+    t_max = max_over_ranks(step_ms, f"cuda:{dev}") if world > 1 else step_ms
+    value = whole_job_rate(pairs, world, t_max)
     pair_kernel_gps = pairs / (pair_ms * 1e-3) / 1e9
 
     # plain FP32 kernel on the same positions, and accuracy of both on sampled sinks
@@ -313,8 +323,11 @@ def run(args):
             gpu_launches=_launches_per_step(w.cpd) * args.steps,
             roofline=dict(bound="alu", achieved=pair_kernel_gps, peak=peak_gps, unit=UNIT,
                           frac=pair_kernel_gps / peak_gps, traffic=None,
+                          paper_convention_frac=pair_kernel_gps * 23 /
+                          (props.multi_processor_count * sm_max * 1e-3 * FP32_LANES_PER_SM * 2),
                           peak_basis=f"FP32 issue roofline: {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
-                                     f"({src}) x 128 lanes / {OPS_PER_PAIR} ops per pair"),
+                                     f"({src}) x 128 lanes / {OPS_PER_PAIR} ops per pair; paper_convention_frac: "
+                                     "23 FLOP per pair against the FMA peak (2 FLOP per lane per cycle)"),
             clocks=clk, e2e=e2e, **extra)
         print(json.dumps(line), flush=True)
     if world > 1:
