@@ -54,6 +54,12 @@ enum nf_status {
     NF_ESTATE = 5    /* call not valid in the box's current state */
 };
 
+/* Pair law (nf_set_softening). */
+enum nf_softening {
+    NF_SPLINE = 0,  /* compact spline of Section 4.3.1 (default); eps = eps_s */
+    NF_PLUMMER = 1  /* F(d) = d / (r^2 + eps_p^2)^(3/2), Eq. (eqn:plummer); eps = eps_p */
+};
+
 /* Accumulation of the per-sink force sums (nf_set_accumulation). */
 enum nf_accumulation {
     NF_ACC_COMPENSATED = 0, /* FP32 partials over blocks of sources, folded with an
@@ -88,6 +94,20 @@ int nf_set_stream(nf_t *nf, void *stream);
 
 /* nf_set_accumulation -- NF_ACC_COMPENSATED (default) or NF_ACC_PLAIN. */
 int nf_set_accumulation(nf_t *nf, int mode);
+
+/*
+ * nf_set_softening -- pair law of later force and adjoint passes: NF_SPLINE
+ * (default) or NF_PLUMMER (Section 4.3.1).  The box's eps is then read as
+ * eps_s or eps_p.  Plummer is not compact, but the near field still covers
+ * only the 125 cells (the far field would carry the rest).  Boxes of one
+ * nf_forces_batched call must share the law.
+ */
+int nf_set_softening(nf_t *nf, int mode);
+
+/* nf_spline_eps_from_plummer -- the spline length with the same minimum
+ * pairwise dynamical time as a Plummer length: eps_s = 2.16 eps_p
+ * (Section 4.3.1). */
+double nf_spline_eps_from_plummer(double eps_plummer);
 
 /*
  * nf_bin_particles -- load particles from global positions (device binning).

@@ -21,13 +21,14 @@ LIB_PATH = os.path.join(_HERE, "libnearfield.so")
 
 NF_OK, NF_EINVAL, NF_ENOMEM, NF_ECUDA, NF_ETIMEOUT, NF_ESTATE = range(6)
 ACC_COMPENSATED, ACC_PLAIN = 0, 1
+SPLINE, PLUMMER = 0, 1
 _STATUS = {1: "NF_EINVAL", 2: "NF_ENOMEM", 3: "NF_ECUDA", 4: "NF_ETIMEOUT", 5: "NF_ESTATE"}
 
 EXPORTS = [
     "nf_create", "nf_destroy", "nf_last_error", "nf_set_stream", "nf_set_accumulation", "nf_bin_particles",
     "nf_set_particles", "nf_set_velocities", "nf_get_particles", "nf_num_particles", "nf_pair_count", "nf_forces",
     "nf_get_forces64", "nf_kick_drift", "nf_vjp", "nf_forces_batched", "nf_profile", "nf_profile_read",
-    "nf_set_shape", "nf_tune", "nf_forces_noalloc",
+    "nf_set_shape", "nf_tune", "nf_forces_noalloc", "nf_set_softening", "nf_spline_eps_from_plummer",
 ]
 
 
@@ -71,6 +72,8 @@ def lib() -> ctypes.CDLL:
             "nf_set_shape": ([p, i, i], i),
             "nf_tune": ([p, ctypes.c_char_p, i], i),
             "nf_forces_noalloc": ([i, d, d, p, p, i64, p, p, ctypes.c_char_p, i], i),
+            "nf_set_softening": ([p, i], i),
+            "nf_spline_eps_from_plummer": ([d], d),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -160,6 +163,10 @@ class NearField:
 
     def set_accumulation(self, mode: int):
         self._call("nf_set_accumulation", int(mode))
+
+    def set_softening(self, mode: int):
+        """SPLINE (compact spline, eps = eps_s) or PLUMMER (eps = eps_p)."""
+        self._call("nf_set_softening", int(mode))
 
     # -------------------------------------------------------------- particles
     def bin_particles(self, xyz):
@@ -257,6 +264,11 @@ class NearField:
         buf = ctypes.create_string_buffer(512)
         self._call("nf_tune", buf, 512)
         return buf.value.decode()
+
+
+def spline_eps_from_plummer(eps_plummer: float) -> float:
+    """eps_s = 2.16 eps_p: equal minimum pairwise dynamical time (Section 4.3.1)."""
+    return float(lib().nf_spline_eps_from_plummer(float(eps_plummer)))
 
 
 def forces_batched(boxes, outs=None):

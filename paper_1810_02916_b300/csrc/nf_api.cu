@@ -38,6 +38,7 @@ struct nf_box {
     int device = 0, sm_count = 0;
     cudaStream_t stream = nullptr;
     int acc_mode = NF_ACC_COMPENSATED;
+    int softening = NF_SPLINE;
     PairShape shape{8, 128, 0};
 
     int64_t n = 0, cap = 0, item_cap = 0;
@@ -350,7 +351,8 @@ int launch_forces(nf_t *nf, const BoxDev *d_boxes, const Item *items, const int 
         nf->ev_used += 2;
         NF_CK(cudaEventRecord(e0, nf->stream));
     }
-    NF_CK(nf::launch_pair(d_boxes, items, n_items, queue, nf->acc_mode == NF_ACC_COMPENSATED, adjoint, nf->shape,
+    NF_CK(nf::launch_pair(d_boxes, items, n_items, queue, nf->acc_mode == NF_ACC_COMPENSATED, adjoint, nf->softening,
+                          nf->shape,
                           nf->sm_count, nf->stream));
     if (nf->profile) NF_CK(cudaEventRecord(e1, nf->stream));
     return NF_OK;
@@ -509,6 +511,16 @@ int nf_set_accumulation(nf_t *nf, int mode)
     nf->acc_mode = mode;
     return NF_OK;
 }
+
+int nf_set_softening(nf_t *nf, int mode)
+{
+    if (!nf) return NF_EINVAL;
+    if (mode != NF_SPLINE && mode != NF_PLUMMER) return fail(nf, NF_EINVAL, "unknown softening mode");
+    nf->softening = mode;
+    return NF_OK;
+}
+
+double nf_spline_eps_from_plummer(double eps_plummer) { return 2.16 * eps_plummer; }
 
 int nf_bin_particles(nf_t *nf, const double *xyz, int64_t n)
 {
@@ -806,8 +818,8 @@ int nf_tune(nf_t *nf, char *report, int report_len)
     char key[160];
     cudaDeviceProp prop;
     NF_CK(cudaGetDeviceProperties(&prop, nf->device));
-    std::snprintf(key, sizeof(key), "%s|cpd=%d|n=%lld|acc=%d", prop.name, nf->cpd, static_cast<long long>(nf->n),
-                  nf->acc_mode);
+    std::snprintf(key, sizeof(key), "%s|cpd=%d|n=%lld|acc=%d|soft=%d", prop.name, nf->cpd,
+                  static_cast<long long>(nf->n), nf->acc_mode, nf->softening);
     std::string summary;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -828,7 +840,7 @@ int nf_tune(nf_t *nf, char *report, int report_len)
         nf->profile = false;
         if ((rc = upload_box(nf, nullptr, nf->acc64, nullptr))) return rc;
         for (const PairShape &s : cand) {
-            if (nf::pair_max_blocks_per_sm(nf->acc_mode == NF_ACC_COMPENSATED, 0, s) < 1) continue;
+            if (nf::pair_max_blocks_per_sm(nf->acc_mode == NF_ACC_COMPENSATED, 0, nf->softening, s) < 1) continue;
             nf->shape = s;
             if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
             NF_CK(cudaEventRecord(a, nf->stream));
@@ -961,6 +973,7 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
         if (!boxes[b]) return fail(nf, NF_EINVAL, "NULL box");
         if (!boxes[b]->have_particles) return fail(nf, NF_ESTATE, "box without particles");
         if (boxes[b]->device != nf->device) return fail(nf, NF_EINVAL, "boxes on different devices");
+        if (boxes[b]->softening != nf->softening) return fail(nf, NF_EINVAL, "boxes with different softening");
     }
     std::lock_guard<std::mutex> lk(g_batch_mu);
     Batch &B = g_batch;

@@ -34,7 +34,7 @@ struct BoxDev {
     int cpd;
     int n;
     float a0, a1, a2;         // spline g(r) = a0 + a1 r + a2 r^2 in cell units
-    float eps2;               // eps^2 in cell units (adjoint branch test)
+    float eps2;               // eps^2 in cell units (spline: adjoint branch test; Plummer: eps_p^2)
     double acc_scale;         // (cpd / box)^2: cell-unit acceleration -> box units
     double grad_scale;        // (cpd / box)^3: cell-unit Jacobian -> box units
 };
@@ -73,9 +73,10 @@ struct PairShape {
 };
 
 // ---- pair kernel (nf_pair.cu) ----
+// softening: 0 = compact spline (Section 4.3.1), 1 = Plummer (Eq. eqn:plummer)
 cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, int compensated,
-                        int adjoint, PairShape shape, int sm_count, cudaStream_t st);
-int pair_max_blocks_per_sm(int compensated, int adjoint, PairShape shape);
+                        int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st);
+int pair_max_blocks_per_sm(int compensated, int adjoint, int softening, PairShape shape);
 
 // ---- scan / sort / binning (nf_sort.cu) ----
 size_t scan_temp_bytes(int64_t n);

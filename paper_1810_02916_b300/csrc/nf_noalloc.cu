@@ -172,7 +172,7 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     NA_CK(cudaMemsetAsync(queue, 0, sizeof(int), st));
     int sms = 0;
     NA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    NA_CK(nf::launch_pair(desc, items, n_items, queue, 1, 0, nf::PairShape{8, 128, 0}, sms, st));
+    NA_CK(nf::launch_pair(desc, items, n_items, queue, 1, 0, 0, nf::PairShape{8, 128, 0}, sms, st));
 #undef NA_CK
     return NF_OK;
 }

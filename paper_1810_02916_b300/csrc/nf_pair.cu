@@ -97,11 +97,27 @@ __device__ __forceinline__ void comp_xor_combine(Comp3 &c, int o)
     two_sum(c.hz, h2, s, e); c.hz = s; c.lz = __fadd_rn(__fadd_rn(c.lz, l2), e);
 }
 
-// one pair: a += f(r) d with f = min(r^-3, a0 + a1 r + a2 r^2)
+// one pair: a += f(r) d.  Spline (SOFT = 0): f = min(r^-3, a0 + a1 r + a2 r^2),
+// 20 FP32-pipe operations + 1 SFU.  Plummer (SOFT = 1, Eq. eqn:plummer):
+// f = (r^2 + eps_p^2)^-3/2, 15 FP32-pipe operations + 1 SFU (eps2 = eps_p^2).
+template <int SOFT>
 __device__ __forceinline__ void pair_force(const float4 q, float xi, float yi, float zi, float &ax, float &ay,
-                                           float &az, float a0, float a1, float a2)
+                                           float &az, float a0, float a1, float a2, float eps2)
 {
     const float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
+    if (SOFT == 1) {
+        const float s2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        float y = rsqrtf(s2);
+        const float t = s2 * y;
+        const float h = t * y;
+        const float e = fmaf(h, -0.5f, 0.5f);
+        y = fmaf(y, e, y);
+        const float f = y * y * y;
+        ax = fmaf(f, dx, ax);
+        ay = fmaf(f, dy, ay);
+        az = fmaf(f, dz, az);
+        return;
+    }
     // + FLT_MIN: below half an ulp of any nonzero r^2 on the 2^-22 grid (r^2 >= 2^-44), so it changes
     // nothing except r = 0 (self pair), where it keeps rsqrt finite: finite g, times d = 0
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, FLT_MIN)));
@@ -120,25 +136,40 @@ __device__ __forceinline__ void pair_force(const float4 q, float xi, float yi, f
 }
 
 // one pair of the adjoint: grad += J(d) (w_j - w_k), J = f I + (f'/r) d d^T
+template <int SOFT>
 __device__ __forceinline__ void pair_adjoint(const float4 q, const float4 wj, float xi, float yi, float zi, float wx,
                                              float wy, float wz, float &gx, float &gy, float &gz, float a0, float a1,
                                              float a2, float eps2)
 {
     const float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
-    float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    const bool inside = r2 < eps2;
-    r2 = fmaxf(r2, FLT_MIN);
-    float y = rsqrtf(r2);
-    const float t = r2 * y;
-    const float h = t * y;
-    const float e = fmaf(h, -0.5f, 0.5f);
-    y = fmaf(y, e, y);
-    const float r = fmaf(t, e, t);
-    const float y2 = y * y;
-    const float y3 = y2 * y;
-    // spline: f = a0 + a1 r + a2 r^2, f'/r = a1 / r + 2 a2 ; Newtonian: f = r^-3, f'/r = -3 r^-5
-    const float f = inside ? fmaf(fmaf(a2, r, a1), r, a0) : y3;
-    const float hh = inside ? fmaf(a1, y, 2.f * a2) : -3.f * y3 * y2;
+    float f, hh;
+    if (SOFT == 1) {
+        // Plummer: f = s^-3/2, f'/r = -3 s^-5/2, s = r^2 + eps_p^2
+        const float s2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        float y = rsqrtf(s2);
+        const float t = s2 * y;
+        const float h = t * y;
+        const float e = fmaf(h, -0.5f, 0.5f);
+        y = fmaf(y, e, y);
+        const float y2 = y * y;
+        f = y2 * y;
+        hh = -3.f * f * y2;
+    } else {
+        float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const bool inside = r2 < eps2;
+        r2 = fmaxf(r2, FLT_MIN);
+        float y = rsqrtf(r2);
+        const float t = r2 * y;
+        const float h = t * y;
+        const float e = fmaf(h, -0.5f, 0.5f);
+        y = fmaf(y, e, y);
+        const float r = fmaf(t, e, t);
+        const float y2 = y * y;
+        const float y3 = y2 * y;
+        // spline: f = a0 + a1 r + a2 r^2, f'/r = a1 / r + 2 a2 ; Newtonian: f = r^-3, f'/r = -3 r^-5
+        f = inside ? fmaf(fmaf(a2, r, a1), r, a0) : y3;
+        hh = inside ? fmaf(a1, y, 2.f * a2) : -3.f * y3 * y2;
+    }
     const float ux = wj.x - wx, uy = wj.y - wy, uz = wj.z - wz;
     const float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
     const float hd = hh * du;
@@ -259,7 +290,7 @@ __device__ __forceinline__ void comp_fold_smem(float *c, float &px, float &py, f
 }
 
 // S = 0: split mode (<= 16 sinks); S = 1, 2, 4: sinks per lane
-template <int S, int B, bool COMP, bool ADJ>
+template <int S, int B, bool COMP, bool ADJ, int SOFT>
 __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, float4 *wstage, int *tstart, int *tpre,
                          float *comp, unsigned char *tslot, int lane)
 {
@@ -323,10 +354,10 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
         if (SPLIT) {
             for (int j = my_split; j < nr; j += splits) {
                 if (ADJ)
-                    pair_adjoint(buf[j], wbuf[j], xi[0], yi[0], zi[0], wx[0], wy[0], wz[0], px[0], py[0], pz[0], a0,
+                    pair_adjoint<SOFT>(buf[j], wbuf[j], xi[0], yi[0], zi[0], wx[0], wy[0], wz[0], px[0], py[0], pz[0], a0,
                                  a1, a2, eps2);
                 else
-                    pair_force(buf[j], xi[0], yi[0], zi[0], px[0], py[0], pz[0], a0, a1, a2);
+                    pair_force<SOFT>(buf[j], xi[0], yi[0], zi[0], px[0], py[0], pz[0], a0, a1, a2, eps2);
             }
         } else {
             constexpr int U = NF_SRC_UNROLL;
@@ -339,12 +370,12 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
                         const float4 wq = wbuf[j + u];
 #pragma unroll
                         for (int s = 0; s < SS; ++s)
-                            pair_adjoint(q, wq, xi[s], yi[s], zi[s], wx[s], wy[s], wz[s], px[s], py[s], pz[s], a0, a1,
+                            pair_adjoint<SOFT>(q, wq, xi[s], yi[s], zi[s], wx[s], wy[s], wz[s], px[s], py[s], pz[s], a0, a1,
                                          a2, eps2);
                     } else {
 #pragma unroll
                         for (int s = 0; s < SS; ++s)
-                            pair_force(q, xi[s], yi[s], zi[s], px[s], py[s], pz[s], a0, a1, a2);
+                            pair_force<SOFT>(q, xi[s], yi[s], zi[s], px[s], py[s], pz[s], a0, a1, a2, eps2);
                     }
                 }
             }
@@ -421,7 +452,7 @@ __host__ __device__ constexpr int per_warp_f4()
     return (ADJ ? 4 : 2) * B + (COMP ? 192 : 0) + 64 + B / 8;
 }
 
-template <int B, bool COMP, bool ADJ>
+template <int B, bool COMP, bool ADJ, int SOFT>
 __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *__restrict__ boxes,
                                                                   const Item *__restrict__ items,
                                                                   const int *__restrict__ n_items_p,
@@ -446,13 +477,13 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
         const BoxDev &bx = boxes[item_box(item)];
         const int cnt = item_count(item);
         if (cnt <= 16)
-            run_item<0, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            run_item<0, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         else if (cnt <= 32)
-            run_item<1, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            run_item<1, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         else if (cnt <= 64)
-            run_item<2, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            run_item<2, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         else
-            run_item<4, B, COMP, ADJ>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            run_item<4, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         __syncwarp();
     }
 }
@@ -466,12 +497,12 @@ size_t smem_bytes(int warps)
 // Occupancy of one instantiation at `warps` warps per block, computed once
 // (the dynamic shared-memory limit is raised once to the 8-warp size), so a
 // launch makes no attribute or occupancy query and can be stream-captured.
-template <int B, bool COMP, bool ADJ>
+template <int B, bool COMP, bool ADJ, int SOFT>
 int blocks_per_sm(int warps)
 {
     static int cache[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
     static bool attr = false;
-    auto kern = pair_kernel<B, COMP, ADJ>;
+    auto kern = pair_kernel<B, COMP, ADJ, SOFT>;
     if (!attr) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem_bytes<B, COMP, ADJ>(8))) != cudaSuccess) {
@@ -492,44 +523,52 @@ int blocks_per_sm(int warps)
     return cache[warps];
 }
 
-template <int B, bool COMP, bool ADJ>
+template <int B, bool COMP, bool ADJ, int SOFT>
 cudaError_t launch_t(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, PairShape shape,
                      int sm_count, cudaStream_t st)
 {
-    const int per_sm = blocks_per_sm<B, COMP, ADJ>(shape.warps);
+    const int per_sm = blocks_per_sm<B, COMP, ADJ, SOFT>(shape.warps);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int blocks = shape.blocks > 0 ? shape.blocks : sm_count * per_sm;
-    pair_kernel<B, COMP, ADJ><<<blocks, shape.warps * 32, smem_bytes<B, COMP, ADJ>(shape.warps), st>>>(boxes, items,
+    pair_kernel<B, COMP, ADJ, SOFT><<<blocks, shape.warps * 32, smem_bytes<B, COMP, ADJ>(shape.warps), st>>>(boxes, items,
                                                                                                       n_items, queue);
     return cudaGetLastError();
 }
 
-template <int B, bool COMP, bool ADJ>
+template <int B, bool COMP, bool ADJ, int SOFT>
 int max_blocks_t(PairShape shape)
 {
-    return blocks_per_sm<B, COMP, ADJ>(shape.warps);
+    return blocks_per_sm<B, COMP, ADJ, SOFT>(shape.warps);
 }
 
 }  // namespace
 
-#define NF_PAIR_DISPATCH(FN, ...)                                                                                   \
+#define NF_PAIR_DISPATCH_S(FN, SOFT, ...)                                                                          \
     do {                                                                                                            \
         if (shape.stage == 256) {                                                                                   \
-            if (adjoint) return compensated ? FN<256, true, true>(__VA_ARGS__) : FN<256, false, true>(__VA_ARGS__); \
-            return compensated ? FN<256, true, false>(__VA_ARGS__) : FN<256, false, false>(__VA_ARGS__);            \
+            if (adjoint)                                                                                            \
+                return compensated ? FN<256, true, true, SOFT>(__VA_ARGS__) : FN<256, false, true, SOFT>(__VA_ARGS__); \
+            return compensated ? FN<256, true, false, SOFT>(__VA_ARGS__) : FN<256, false, false, SOFT>(__VA_ARGS__); \
         }                                                                                                           \
-        if (adjoint) return compensated ? FN<128, true, true>(__VA_ARGS__) : FN<128, false, true>(__VA_ARGS__);     \
-        return compensated ? FN<128, true, false>(__VA_ARGS__) : FN<128, false, false>(__VA_ARGS__);                \
+        if (adjoint)                                                                                                \
+            return compensated ? FN<128, true, true, SOFT>(__VA_ARGS__) : FN<128, false, true, SOFT>(__VA_ARGS__);  \
+        return compensated ? FN<128, true, false, SOFT>(__VA_ARGS__) : FN<128, false, false, SOFT>(__VA_ARGS__);    \
+    } while (0)
+
+#define NF_PAIR_DISPATCH(FN, ...)                                                                                   \
+    do {                                                                                                            \
+        if (softening == 1) NF_PAIR_DISPATCH_S(FN, 1, __VA_ARGS__);                                                 \
+        NF_PAIR_DISPATCH_S(FN, 0, __VA_ARGS__);                                                                     \
     } while (0)
 
 cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, int compensated,
-                        int adjoint, PairShape shape, int sm_count, cudaStream_t st)
+                        int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st)
 {
     if (shape.warps < 1 || shape.warps > 8 || (shape.stage != 128 && shape.stage != 256)) return cudaErrorInvalidValue;
     NF_PAIR_DISPATCH(launch_t, boxes, items, n_items, queue, shape, sm_count, st);
 }
 
-int pair_max_blocks_per_sm(int compensated, int adjoint, PairShape shape)
+int pair_max_blocks_per_sm(int compensated, int adjoint, int softening, PairShape shape)
 {
     if (shape.warps < 1 || shape.warps > 8 || (shape.stage != 128 && shape.stage != 256)) return 0;
     NF_PAIR_DISPATCH(max_blocks_t, shape);

@@ -70,3 +70,12 @@ def test_null_handles_are_rejected(libnf):
     assert L.nf_forces(None, None) == nfb.NF_EINVAL
     assert L.nf_kick_drift(None, 0.1) == nfb.NF_EINVAL
     L.nf_destroy(None)
+
+
+def test_plummer_to_spline_length_is_the_printed_factor(libnf):
+    """Section 4.3.1: eps_s = 2.16 eps_p (host-only helper, no GPU)."""
+    import json
+    import os
+    import paper_1810_02916_b300 as nfb
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "spline_law.json")))
+    assert nfb.spline_eps_from_plummer(0.01) == pytest.approx(g["eps_s_over_eps_p"] * 0.01, rel=1e-15)

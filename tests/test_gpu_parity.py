@@ -259,3 +259,38 @@ def test_kick_drift_requires_forces_and_respects_drift_limit():
     assert e.value.code == nfb.NF_EINVAL
     st1 = nf.get_particles()
     assert np.array_equal(st0["pos"], st1["pos"]) and np.array_equal(st0["perm"], st1["perm"])
+
+
+# ------------------------------------------------------------------ Plummer softening (Eq. eqn:plummer)
+
+@pytest.mark.parametrize("name", ["uniform32k", "clustered64"])
+def test_plummer_forces_match_oracle(name):
+    import paper_1810_02916_b300 as nfb
+    w = workload(name)
+    eps_p = w.eps / 2.16
+    nf = nfb.NearField(w.cpd, eps_p)
+    nf.set_softening(nfb.PLUMMER)
+    nf.bin_particles(w.pos)
+    acc = nf.forces()
+    b = oracle_side(w.pos, w.cpd)
+    ref, sa, _ = oracle.forces(b, eps_p, soft=oracle.PLUMMER, with_sumabs=True)
+    _check_forces(acc, ref, sa)
+    # the spline pass of the same box differs (the laws differ inside eps)
+    nf.set_softening(nfb.SPLINE)
+    assert not np.array_equal(nf.forces(), acc)
+
+
+def test_plummer_adjoint_matches_oracle():
+    import paper_1810_02916_b300 as nfb
+    w = workload("clustered64")
+    nf = nfb.NearField(w.cpd, w.eps / 2.16)
+    nf.set_softening(nfb.PLUMMER)
+    nf.bin_particles(w.pos)
+    W = np.zeros((nf.n, 4), np.float32)
+    W[:, :3] = gen.cotangent(nf.n, np.random.default_rng(31)).astype(np.float32)
+    g = nf.vjp(W)
+    b = oracle_side(w.pos, w.cpd)
+    sinks = sample_sinks(b, 20000)
+    ref = oracle.vjp(b, w.eps / 2.16, W[:, :3].astype(np.float64), sinks, soft=oracle.PLUMMER)
+    s = oracle.error_stats(g[sinks, :3], ref)
+    assert s["rms_rel"] <= 1e-5, s
