@@ -44,6 +44,9 @@ namespace {
 #ifndef NF_SRC_UNROLL
 #define NF_SRC_UNROLL 8   // staged sources evaluated per unrolled step of the broadcast loop
 #endif
+#ifndef NF_STAGE_A
+#define NF_STAGE_A 128   // sources staged per round for the launch shape's stage = 128
+#endif
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
@@ -551,8 +554,10 @@ int max_blocks_t(PairShape shape)
             return compensated ? FN<256, true, false, SOFT>(__VA_ARGS__) : FN<256, false, false, SOFT>(__VA_ARGS__); \
         }                                                                                                           \
         if (adjoint)                                                                                                \
-            return compensated ? FN<128, true, true, SOFT>(__VA_ARGS__) : FN<128, false, true, SOFT>(__VA_ARGS__);  \
-        return compensated ? FN<128, true, false, SOFT>(__VA_ARGS__) : FN<128, false, false, SOFT>(__VA_ARGS__);    \
+            return compensated ? FN<NF_STAGE_A, true, true, SOFT>(__VA_ARGS__)                                      \
+                               : FN<NF_STAGE_A, false, true, SOFT>(__VA_ARGS__);                                    \
+        return compensated ? FN<NF_STAGE_A, true, false, SOFT>(__VA_ARGS__)                                         \
+                           : FN<NF_STAGE_A, false, false, SOFT>(__VA_ARGS__);                                       \
     } while (0)
 
 #define NF_PAIR_DISPATCH(FN, ...)                                                                                   \
