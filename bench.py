@@ -40,6 +40,11 @@ WORKLOAD = "zeldovich512"
 METRIC = "near-field Gpair-interactions/s and particles/s/step at 512^3 clustered vs plain FP32 kernel"
 UNIT = "Gpair/s"
 OPS_PER_PAIR = 20          # FP32-pipe operations of the pair arithmetic (issue roofline)
+# DRAM bytes (read + write) of one compensated pair-kernel launch of this workload, from the ncu
+# launch list in profiles/launches_zeldovich512_bench.md, valid while nf_pair.cu hashes to the value
+# below (the record reports null traffic once the kernel source has changed)
+PAIR_TRAFFIC_BYTES = 8.9598e9
+PAIR_TRAFFIC_SOURCE_SHA256 = "2fa77977148069df"
 FP32_LANES_PER_SM = 128
 
 
@@ -173,6 +178,13 @@ def max_over_ranks(x: float, device: str = "cpu") -> float:
 def whole_job_rate(pairs_per_replica: int, world: int, step_ms: float) -> float:
     """Gpair/s of the whole job: every rank evaluates its own replica in step_ms (the slowest rank's time)."""
     return world * pairs_per_replica / (step_ms * 1e-3) / 1e9
+
+
+def _pair_traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_1810_02916_b300", "csrc", "nf_pair.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return PAIR_TRAFFIC_BYTES if h == PAIR_TRAFFIC_SOURCE_SHA256 else None
 
 
 def _launches_per_step(cpd):
@@ -322,7 +334,9 @@ def run(args):
             particles_per_s_per_step=world * n / (t_max * 1e-3),
             gpu_launches=_launches_per_step(w.cpd) * args.steps,
             roofline=dict(bound="alu", achieved=pair_kernel_gps, peak=peak_gps, unit=UNIT,
-                          frac=pair_kernel_gps / peak_gps, traffic=None,
+                          frac=pair_kernel_gps / peak_gps, traffic=_pair_traffic(),
+                          traffic_note="DRAM read+write bytes of one pair-kernel launch (ncu, same workload); "
+                                       "algorithmic bytes: positions 2.15 GB read + FP64 sums 3.22 GB written",
                           paper_convention_frac=pair_kernel_gps * 23 /
                           (props.multi_processor_count * sm_max * 1e-3 * FP32_LANES_PER_SM * 2),
                           peak_basis=f"FP32 issue roofline: {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
