@@ -187,6 +187,22 @@ int nf_get_forces64(nf_t *nf, double *acc);
 int nf_kick_drift(nf_t *nf, double dt);
 
 /*
+ * nf_choose_dt -- global time step from the criteria of Section 4.2.1, using
+ * the box's velocities and the accelerations of the last nf_forces:
+ *   dt_acc   = eta * max( min over cells of v_rms,c / a_max,c ,  v_rms / a_max )
+ *              (v_rms = sqrt(mean |v|^2), a_max = max |a|; per cell and over
+ *              all particles; cells with a_max = 0 are skipped; the global
+ *              value guards against abnormally cold cells)
+ *   dt_drift = 0.8 cell widths / max |v|
+ *   dt       = min(dt_max, dt_acc, dt_drift)
+ * dt_max stands in for the TimeStepDlna cap of an expanding box.  eta is
+ * TimeStepAccel (the paper uses 0.15 and 0.3).  parts (may be NULL) receives
+ * {dt_acc, dt_drift, dt_max}.  With all velocities zero dt_acc is 0.
+ * NF_ESTATE without a previous nf_forces.  Synchronises.
+ */
+int nf_choose_dt(nf_t *nf, double eta, double dt_max, double *dt, double *parts);
+
+/*
  * nf_vjp -- adjoint (vector-Jacobian product) of the accelerations.
  *   w     n x 4 floats (cotangent w_k, storage order; 4th ignored)
  *   grad  n x 4 floats out: d(sum_i w_i . a_i)/dx_k in box units

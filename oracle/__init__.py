@@ -223,6 +223,31 @@ def kick_drift(X: np.ndarray, V: np.ndarray, A: np.ndarray, dt: float, box: floa
     return X, V
 
 
+def choose_dt(b: Binned, V: np.ndarray, A: np.ndarray, eta: float, dt_max: float):
+    """Global time step of Section 4.2.1 (storage-order velocities V and accelerations A, box units).
+
+    dt_acc = eta * max(min over cells of v_rms,c / a_max,c, v_rms / a_max) with
+    v_rms = sqrt(mean |v|^2) and a_max = max |a| (cells with a_max = 0 skipped);
+    dt_drift = 0.8 cell widths / max |v|; dt = min(dt_max, dt_acc, dt_drift).
+    """
+    V = np.asarray(V, dtype=np.float64)
+    A = np.asarray(A, dtype=np.float64)
+    ratio_min = np.inf
+    for c in np.flatnonzero(b.counts):
+        lo, hi = b.offsets[c], b.offsets[c + 1]
+        amax = np.sqrt((A[lo:hi] ** 2).sum(axis=1).max())
+        if amax > 0:
+            vrms = np.sqrt((V[lo:hi] ** 2).sum(axis=1).mean())
+            ratio_min = min(ratio_min, vrms / amax)
+    vrms_g = np.sqrt((V ** 2).sum(axis=1).mean()) if len(V) else 0.0
+    amax_g = np.sqrt((A ** 2).sum(axis=1).max()) if len(A) else 0.0
+    glob = vrms_g / amax_g if amax_g > 0 else np.inf
+    dt_acc = eta * max(ratio_min, glob)
+    vmax = np.sqrt((V ** 2).sum(axis=1).max()) if len(V) else 0.0
+    dt_drift = 0.8 * b.w / vmax if vmax > 0 else np.inf
+    return min(dt_max, dt_acc, dt_drift), dict(dt_acc=dt_acc, dt_drift=dt_drift, dt_max=dt_max)
+
+
 # ---------------------------------------------------------------- errors
 
 def error_stats(a_test: np.ndarray, a_ref: np.ndarray, sumabs: np.ndarray | None = None) -> dict:

@@ -29,6 +29,7 @@ EXPORTS = [
     "nf_set_particles", "nf_set_velocities", "nf_get_particles", "nf_num_particles", "nf_pair_count", "nf_forces",
     "nf_get_forces64", "nf_kick_drift", "nf_vjp", "nf_forces_batched", "nf_profile", "nf_profile_read",
     "nf_set_shape", "nf_tune", "nf_forces_noalloc", "nf_set_softening", "nf_spline_eps_from_plummer",
+    "nf_choose_dt",
 ]
 
 
@@ -73,6 +74,7 @@ def lib() -> ctypes.CDLL:
             "nf_tune": ([p, ctypes.c_char_p, i], i),
             "nf_forces_noalloc": ([i, d, d, p, p, i64, p, p, ctypes.c_char_p, i], i),
             "nf_set_softening": ([p, i], i),
+            "nf_choose_dt": ([p, d, d, ctypes.POINTER(d), ctypes.POINTER(d)], i),
             "nf_spline_eps_from_plummer": ([d], d),
         }
         for name, (args, res) in sig.items():
@@ -224,6 +226,13 @@ class NearField:
         if isinstance(out, np.ndarray):
             self.synchronize()
         return out
+
+    def choose_dt(self, eta: float, dt_max: float):
+        """(dt, {dt_acc, dt_drift, dt_max}) from the time-step criteria (Section 4.2.1)."""
+        dt = ctypes.c_double()
+        parts = (ctypes.c_double * 3)()
+        self._call("nf_choose_dt", float(eta), float(dt_max), ctypes.byref(dt), parts)
+        return float(dt.value), dict(dt_acc=parts[0], dt_drift=parts[1], dt_max=parts[2])
 
     def kick_drift(self, dt: float):
         self._call("nf_kick_drift", float(dt))

@@ -71,6 +71,7 @@ struct nf_box {
     const int *h_nbr = nullptr;
     long long wf = 0;                 // resident warps (<= 32 per SM) x balance factor 4
     int reduce_cap = 0;
+    void *dt_tmp = nullptr;           // time-step reductions
     unsigned long long *pairs = nullptr;
     BoxDev *d_box = nullptr;
     BoxDev h_box{};                   // host mirror of *d_box
@@ -454,6 +455,7 @@ int nf_create(int cpd, int R, double eps, double box, nf_t **out)
         (rc = dalloc(nf, &nf->n_items, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->queue, sizeof(int) * 4)) ||
         (rc = dalloc(nf, &nf->n_raw, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->n_reduce, sizeof(int) * 4)) ||
         (rc = dalloc(nf, &nf->nbr_ptr, sizeof(int *))) ||
+        (rc = dalloc(nf, &nf->dt_tmp, nf::dt_temp_bytes(nf->ncell))) ||
         (rc = dalloc(nf, &nf->err, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->pairs, sizeof(unsigned long long))) ||
         (rc = dalloc(nf, &nf->d_box, sizeof(BoxDev)))) {
         g_create_error = nf->last_error;
@@ -486,6 +488,7 @@ void nf_destroy(nf_t *nf)
     if (nf->scan_tmp) cudaFree(nf->scan_tmp);
     dfree(nf->n_items); dfree(nf->queue); dfree(nf->err); dfree(nf->pairs); dfree(nf->d_box);
     dfree(nf->n_raw); dfree(nf->n_reduce); dfree(nf->nbr_ptr);
+    if (nf->dt_tmp) cudaFree(nf->dt_tmp);
     if (nf->stage.p) cudaFree(nf->stage.p);
     for (cudaEvent_t e : nf->ev) cudaEventDestroy(e);
     delete nf;
@@ -773,6 +776,34 @@ int nf_kick_drift(nf_t *nf, double dt)
     nf->generation = ++g_generation;
     nf->have_forces = false;
     NF_CK(cudaStreamSynchronize(nf->stream));
+    return NF_OK;
+}
+
+int nf_choose_dt(nf_t *nf, double eta, double dt_max, double *dt, double *parts)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (!dt) return fail(nf, NF_EINVAL, "dt is NULL");
+    if (!(eta > 0) || !(dt_max > 0)) return fail(nf, NF_EINVAL, "eta and dt_max must be positive");
+    if (!nf->have_forces) return fail(nf, NF_ESTATE, "nf_choose_dt needs a previous nf_forces");
+    double h[4] = {INFINITY, 0.0, 0.0, 0.0};
+    if (nf->n > 0) {
+        NF_CK(nf::dt_reduce(nf->cell_start, nf->ncell, nf->vel, nf->acc64, nf->dt_tmp, nf->stream));
+        NF_CK(cudaMemcpyAsync(h, nf->dt_tmp, sizeof(h), cudaMemcpyDeviceToHost, nf->stream));
+        NF_CK(cudaStreamSynchronize(nf->stream));
+    }
+    // Section 4.2.1: eta times the larger of (smallest cell v_rms / a_max) and the global v_rms / a_max;
+    // a drift of at most 0.8 cell widths; and a cap (TimeStepDlna in an expanding box)
+    const double v_rms = nf->n > 0 ? std::sqrt(h[1] / static_cast<double>(nf->n)) : 0.0;
+    const double global = h[2] > 0 ? v_rms / h[2] : INFINITY;
+    const double dt_acc = eta * std::max(h[0], global);
+    const double dt_drift = h[3] > 0 ? 0.8 * nf->w / h[3] : INFINITY;
+    *dt = std::min(dt_max, std::min(dt_acc, dt_drift));
+    if (parts) {
+        parts[0] = dt_acc;
+        parts[1] = dt_drift;
+        parts[2] = dt_max;
+    }
     return NF_OK;
 }
 

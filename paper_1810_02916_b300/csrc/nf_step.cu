@@ -85,3 +85,111 @@ cudaError_t drift(const float4 *pos, const float4 *vel_new, const uint32_t *cell
 }
 
 }  // namespace nf
+
+// ---------------------------------------------------------------- time step (Section 4.2.1)
+//
+// Per cell: v_rms = sqrt(mean |v|^2) and a_max = max |a| over its particles;
+// per pass: the minimum over cells of v_rms / a_max (cells with a_max = 0
+// skipped), the global sum of |v|^2, max |a| and max |v|.  Blocks write their
+// partial results; one block combines them in a fixed order, so the result
+// does not depend on scheduling.
+
+namespace nf {
+namespace {
+
+constexpr int kDtThreads = 256;
+
+struct DtPart {
+    double ratio_min;   // min over cells of v_rms / a_max
+    double v2_sum;      // sum of |v|^2
+    double a_max;       // max |a|
+    double v_max;       // max |v|
+};
+
+__global__ void dt_cells(const int *__restrict__ cell_start, int ncell, const float4 *__restrict__ vel,
+                         const double *__restrict__ acc64, DtPart *__restrict__ parts)
+{
+    __shared__ DtPart sh[kDtThreads];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    DtPart p{INFINITY, 0.0, 0.0, 0.0};
+    if (c < ncell) {
+        const int s0 = cell_start[c], s1 = cell_start[c + 1];
+        double v2 = 0.0, am = 0.0, vm = 0.0;
+        for (int k = s0; k < s1; ++k) {
+            const float4 v = vel[k];
+            const double vv = static_cast<double>(v.x) * v.x + static_cast<double>(v.y) * v.y +
+                              static_cast<double>(v.z) * v.z;
+            const double *a = acc64 + 3 * static_cast<int64_t>(k);
+            const double aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+            v2 += vv;
+            am = fmax(am, aa);
+            vm = fmax(vm, vv);
+        }
+        if (s1 > s0) {
+            am = sqrt(am);
+            if (am > 0.0) p.ratio_min = sqrt(v2 / (s1 - s0)) / am;
+            p.v2_sum = v2;
+            p.a_max = am;
+            p.v_max = sqrt(vm);
+        }
+    }
+    sh[threadIdx.x] = p;
+    __syncthreads();
+    for (int o = kDtThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            DtPart &a = sh[threadIdx.x];
+            const DtPart &b = sh[threadIdx.x + o];
+            a.ratio_min = fmin(a.ratio_min, b.ratio_min);
+            a.v2_sum += b.v2_sum;
+            a.a_max = fmax(a.a_max, b.a_max);
+            a.v_max = fmax(a.v_max, b.v_max);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) parts[blockIdx.x] = sh[0];
+}
+
+__global__ void dt_combine(const DtPart *__restrict__ parts, int nparts, DtPart *__restrict__ out)
+{
+    __shared__ DtPart sh[kDtThreads];
+    DtPart p{INFINITY, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        const DtPart q = parts[i];
+        p.ratio_min = fmin(p.ratio_min, q.ratio_min);
+        p.v2_sum += q.v2_sum;
+        p.a_max = fmax(p.a_max, q.a_max);
+        p.v_max = fmax(p.v_max, q.v_max);
+    }
+    sh[threadIdx.x] = p;
+    __syncthreads();
+    for (int o = kDtThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            DtPart &a = sh[threadIdx.x];
+            const DtPart &b = sh[threadIdx.x + o];
+            a.ratio_min = fmin(a.ratio_min, b.ratio_min);
+            a.v2_sum += b.v2_sum;
+            a.a_max = fmax(a.a_max, b.a_max);
+            a.v_max = fmax(a.v_max, b.v_max);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+}  // namespace
+
+size_t dt_temp_bytes(int ncell) { return sizeof(DtPart) * (static_cast<size_t>((ncell + kDtThreads - 1) / kDtThreads) + 1); }
+
+// result: 4 doubles {min over cells of v_rms/a_max, sum |v|^2, max |a|, max |v|} at temp[0..3]
+cudaError_t dt_reduce(const int *cell_start, int ncell, const float4 *vel, const double *acc64, void *temp,
+                      cudaStream_t st)
+{
+    const int nb = (ncell + kDtThreads - 1) / kDtThreads;
+    DtPart *out = static_cast<DtPart *>(temp);
+    DtPart *parts = out + 1;
+    dt_cells<<<nb, kDtThreads, 0, st>>>(cell_start, ncell, vel, acc64, parts);
+    dt_combine<<<1, kDtThreads, 0, st>>>(parts, nb, out);
+    return cudaGetLastError();
+}
+
+}  // namespace nf

@@ -244,3 +244,22 @@ def test_full_size_sampled_parity(name):
     s = oracle.error_stats(acc[sinks, :3], ref, sa)
     assert s["rms_rel"] <= RMS_TOL and s["max_bound_ratio"] <= BOUND_K, s
     assert nf.pair_count() == oracle.pair_count(b)
+
+
+def test_choose_dt_matches_oracle():
+    cpd, eps = 8, 2e-3
+    rng = np.random.default_rng(41)
+    X, _ = gen.clustered(30000, rng, 4, 0.05, 0.2)
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    V = rng.standard_normal((nf.n, 3)).astype(np.float32)
+    vel = np.zeros((nf.n, 4), np.float32)
+    vel[:, :3] = V
+    nf.set_velocities(vel)
+    nf.forces(False)
+    dt, parts = nf.choose_dt(0.15, 1.0)
+    A = oracle.forces(b, eps)
+    dto, po = oracle.choose_dt(b, V.astype(np.float64), A, 0.15, 1.0)
+    assert dt == pytest.approx(dto, rel=1e-5)
+    for k in ("dt_acc", "dt_drift", "dt_max"):
+        assert parts[k] == pytest.approx(po[k], rel=1e-5)

@@ -339,3 +339,25 @@ def test_error_stats_definitions():
     assert s["median"] == pytest.approx(1e-6)
     assert s["frac_gt_1e-4"] == pytest.approx(1 / 3)
     assert s["max_bound_ratio"] == pytest.approx(4e-3 * 2 ** 24)
+
+
+# ------------------------------------------------------------------ time step (Section 4.2.1)
+
+def test_time_step_criteria_on_a_hand_worked_case():
+    """Two cells, values worked out by hand from the three criteria of Section 4.2.1."""
+    cpd, box = 5, 1.0
+    X = np.array([[0.01, 0.01, 0.01], [0.02, 0.01, 0.01], [0.5, 0.5, 0.5]])
+    b = oracle.bin_positions(X, cpd, box)
+    V = np.array([[1.0, 0, 0], [0, 2.0, 0], [0, 0, 0.1]])[b.order]
+    A = np.array([[3.0, 0, 0], [0, 4.0, 0], [0, 0, 10.0]])[b.order]
+    dt, parts = oracle.choose_dt(b, V, A, eta=0.15, dt_max=1.0)
+    # cell of the first two: v_rms = sqrt(2.5), a_max = 4; the lone cold particle: 0.1 / 10
+    # global: sqrt(5.01 / 3) / 10 = 0.12923 > 0.01, so the global value wins
+    assert parts["dt_acc"] == pytest.approx(0.15 * math.sqrt(5.01 / 3) / 10.0, rel=1e-14)
+    assert parts["dt_drift"] == pytest.approx(0.8 * 0.2 / 2.0, rel=1e-14)
+    assert dt == pytest.approx(min(1.0, parts["dt_acc"], parts["dt_drift"]))
+    # a hot, fast-accelerating cell: the cell criterion decides
+    A2 = A.copy()
+    A2[:] = [[0, 0, 0.01]] * 3
+    _, p2 = oracle.choose_dt(b, V, A2, eta=0.3, dt_max=1.0)
+    assert p2["dt_acc"] == pytest.approx(0.3 * math.sqrt(5.01 / 3) / 0.01, rel=1e-14)
