@@ -448,6 +448,31 @@ def run_adjoint(args):
     return 0
 
 
+def run_multipoles(args):
+    """Secondary measurement: order-8 Cartesian multipoles of every cell of the 256^3 clustered box."""
+    import torch
+    import paper_1810_02916_b300 as nfb
+    w = _make_workload("clustered256")
+    nf = nfb.NearField(w.cpd, w.eps, w.box)
+    nf.bin_particles(torch.from_numpy(w.pos).cuda())
+    T = 165
+    out = torch.empty((nf.ncell, T), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        nf.multipoles(8, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        nf.multipoles(8, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps(dict(mode="multipoles", workload="clustered256", order=8, cells=nf.ncell, particles=nf.n,
+                          ms=ms, mparticles_s=nf.n / (ms * 1e-3) / 1e6,
+                          out_gb=nf.ncell * T * 8 / 1e9)), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -462,13 +487,15 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, help="profiling driver only (with --forces-only)")
     ap.add_argument("--forces-only", type=int, default=0, help="profiling driver: this many force passes")
     ap.add_argument("--plain", action="store_true", help="profiling driver: plain FP32 accumulation")
-    ap.add_argument("--mode", default="step", choices=["step", "batched", "adjoint"],
+    ap.add_argument("--mode", default="step", choices=["step", "batched", "adjoint", "multipoles"],
                     help="batched / adjoint: secondary measurements (not the bench line)")
     args = ap.parse_args()
     if args.mode == "batched":
         return run_batched(args)
     if args.mode == "adjoint":
         return run_adjoint(args)
+    if args.mode == "multipoles":
+        return run_multipoles(args)
     if args.forces_only:
         return run_forces_only(args)
     if args.impl == "reference":

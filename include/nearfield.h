@@ -203,6 +203,18 @@ int nf_kick_drift(nf_t *nf, double dt);
 int nf_choose_dt(nf_t *nf, double eta, double dt_max, double *dt, double *parts);
 
 /*
+ * nf_multipoles -- Cartesian multipole moments of every cell, the per-cell
+ * step the far field starts from (Section 2.1; order p = 8 in the paper):
+ *   M_c[a, b, k] = sum over the cell's particles of x^a y^b z^k,
+ *   a + b + k <= order (0..8), x = offset from the cell centre in cell widths,
+ *   unit masses, FP64 arithmetic (the paper computes multipoles in double).
+ *   out  cpd^3 x T doubles, T = (p+1)(p+2)(p+3)/6 (165 at p = 8), cell-major;
+ *        terms ordered by degree n, then a = n..0, then b = n-a..0.
+ * Host or device pointer.  (async for device out)
+ */
+int nf_multipoles(nf_t *nf, int order, double *out);
+
+/*
  * nf_vjp -- adjoint (vector-Jacobian product) of the accelerations.
  *   w     n x 4 floats (cotangent w_k, storage order; 4th ignored)
  *   grad  n x 4 floats out: d(sum_i w_i . a_i)/dx_k in box units

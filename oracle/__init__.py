@@ -223,6 +223,24 @@ def kick_drift(X: np.ndarray, V: np.ndarray, A: np.ndarray, dt: float, box: floa
     return X, V
 
 
+def multipole_terms(order: int):
+    """(a, b, k) of every term, by degree n, then a = n..0, then b = n-a..0."""
+    return [(a, b, n - a - b) for n in range(order + 1) for a in range(n, -1, -1) for b in range(n - a, -1, -1)]
+
+
+def multipoles(bn: Binned, order: int = 8) -> np.ndarray:
+    """Cartesian moments M_c[a, b, k] = sum_i x^a y^b z^k of every cell (Section 2.1), FP64.
+
+    x = offset from the cell centre in cell widths, unit masses; (cpd^3, T) array.
+    """
+    terms = multipole_terms(order)
+    x = bn.xq.astype(np.float64)
+    out = np.zeros((bn.cpd ** 3, len(terms)))
+    for t, (a, b, k) in enumerate(terms):
+        np.add.at(out[:, t], bn.cell, x[:, 0] ** a * x[:, 1] ** b * x[:, 2] ** k)
+    return out
+
+
 def choose_dt(b: Binned, V: np.ndarray, A: np.ndarray, eta: float, dt_max: float):
     """Global time step of Section 4.2.1 (storage-order velocities V and accelerations A, box units).
 

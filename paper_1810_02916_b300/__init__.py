@@ -29,7 +29,7 @@ EXPORTS = [
     "nf_set_particles", "nf_set_velocities", "nf_get_particles", "nf_num_particles", "nf_pair_count", "nf_forces",
     "nf_get_forces64", "nf_kick_drift", "nf_vjp", "nf_forces_batched", "nf_profile", "nf_profile_read",
     "nf_set_shape", "nf_tune", "nf_forces_noalloc", "nf_set_softening", "nf_spline_eps_from_plummer",
-    "nf_choose_dt",
+    "nf_choose_dt", "nf_multipoles",
 ]
 
 
@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
             "nf_forces_noalloc": ([i, d, d, p, p, i64, p, p, ctypes.c_char_p, i], i),
             "nf_set_softening": ([p, i], i),
             "nf_choose_dt": ([p, d, d, ctypes.POINTER(d), ctypes.POINTER(d)], i),
+            "nf_multipoles": ([p, i, p], i),
             "nf_spline_eps_from_plummer": ([d], d),
         }
         for name, (args, res) in sig.items():
@@ -233,6 +234,15 @@ class NearField:
         parts = (ctypes.c_double * 3)()
         self._call("nf_choose_dt", float(eta), float(dt_max), ctypes.byref(dt), parts)
         return float(dt.value), dict(dt_acc=parts[0], dt_drift=parts[1], dt_max=parts[2])
+
+    def multipoles(self, order: int = 8, out=None):
+        """Cartesian multipole moments of every cell, (cpd^3, (p+1)(p+2)(p+3)/6) float64, cell units."""
+        T = (order + 1) * (order + 2) * (order + 3) // 6
+        if out is None:
+            out = np.empty((self.ncell, T), np.float64)
+        _check_arr(out, np.float64, (self.ncell, T), "out")
+        self._call("nf_multipoles", int(order), _ptr(out))
+        return out
 
     def kick_drift(self, dt: float):
         self._call("nf_kick_drift", float(dt))

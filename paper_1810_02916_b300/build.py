@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libnearfield.so")
 OBJ = os.path.join(ROOT, "_build", "obj")
-SOURCES = ["nf_pair.cu", "nf_sort.cu", "nf_plan.cu", "nf_step.cu", "nf_api.cu", "nf_noalloc.cu"]
+SOURCES = ["nf_pair.cu", "nf_sort.cu", "nf_plan.cu", "nf_step.cu", "nf_api.cu", "nf_noalloc.cu", "nf_multipole.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include")]

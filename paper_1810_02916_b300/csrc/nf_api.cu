@@ -807,6 +807,21 @@ int nf_choose_dt(nf_t *nf, double eta, double dt_max, double *dt, double *parts)
     return NF_OK;
 }
 
+int nf_multipoles(nf_t *nf, int order, double *out)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (order < 0 || order > 8) return fail(nf, NF_EINVAL, "multipole order must be 0..8");
+    if (!out) return fail(nf, NF_EINVAL, "out is NULL");
+    if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
+    const size_t bytes = sizeof(double) * static_cast<size_t>(nf->ncell) * nf::multipole_terms(order);
+    return produce_out(nf, out, bytes, [&](void *d) -> int {
+        NF_CK(nf::cell_multipoles(nf->cell_start, nf->ncell, nf->pos, order, static_cast<double *>(d), nf->sm_count,
+                                  nf->stream));
+        return NF_OK;
+    });
+}
+
 int nf_profile(nf_t *nf, int enable)
 {
     if (!nf) return NF_EINVAL;

@@ -123,6 +123,11 @@ cudaError_t drift(const float4 *pos, const float4 *vel_new, const uint32_t *cell
                   double dt, double inv_w, int cpd, int n, uint32_t *key_by_id, uint32_t *val_by_id,
                   float4 *xq_by_id, float4 *vel_by_id, cudaStream_t st);
 
+// cell multipoles (nf_multipole.cu)
+int multipole_terms(int order);
+cudaError_t cell_multipoles(const int *cell_start, int ncell, const float4 *pos, int order, double *out, int sm_count,
+                            cudaStream_t st);
+
 // time-step criteria (nf_step.cu)
 size_t dt_temp_bytes(int ncell);
 cudaError_t dt_reduce(const int *cell_start, int ncell, const float4 *vel, const double *acc64, void *temp,

@@ -263,3 +263,15 @@ def test_choose_dt_matches_oracle():
     assert dt == pytest.approx(dto, rel=1e-5)
     for k in ("dt_acc", "dt_drift", "dt_max"):
         assert parts[k] == pytest.approx(po[k], rel=1e-5)
+
+
+@pytest.mark.parametrize("order", [0, 3, 8])
+def test_cell_multipoles_match_oracle(order):
+    w = workload("clustered64")
+    nf = make_box(w.pos, w.cpd, w.eps)
+    b = oracle_side(w.pos, w.cpd)
+    M = nf.multipoles(order)
+    ref = oracle.multipoles(b, order)
+    tol = 1e-13 * b.counts.astype(np.float64)[:, None] + 1e-12 * np.abs(ref)
+    assert np.all(np.abs(M - ref) <= tol)
+    assert np.array_equal(M[:, 0], b.counts.astype(np.float64))

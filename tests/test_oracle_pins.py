@@ -361,3 +361,53 @@ def test_time_step_criteria_on_a_hand_worked_case():
     A2[:] = [[0, 0, 0.01]] * 3
     _, p2 = oracle.choose_dt(b, V, A2, eta=0.3, dt_max=1.0)
     assert p2["dt_acc"] == pytest.approx(0.3 * math.sqrt(5.01 / 3) / 0.01, rel=1e-14)
+
+
+# ------------------------------------------------------------------ cell multipoles (Section 2.1)
+
+def test_multipoles_of_one_particle_are_its_monomials():
+    X = np.array([[0.13, 0.71, 0.44]])
+    b = oracle.bin_positions(X, 5)
+    M = oracle.multipoles(b, 8)
+    x, y, z = (float(v) for v in b.xq[0])
+    c = int(b.cell[0])
+    for t, (a, bb, k) in enumerate(oracle.multipole_terms(8)):
+        assert M[c, t] == pytest.approx(math.pow(x, a) * math.pow(y, bb) * math.pow(z, k), rel=1e-14, abs=1e-300)
+    assert len(oracle.multipole_terms(8)) == 165
+    assert np.count_nonzero(np.abs(M).sum(axis=1)) == 1
+
+
+def test_multipoles_obey_the_shift_theorem():
+    """Moments about a shifted origin follow from the binomial expansion of (x + s)^a."""
+    rng = np.random.default_rng(17)
+    X = rng.random((400, 3)) * 0.2 + 0.4                     # all in one cell of a CPD 5 grid
+    b = oracle.bin_positions(X, 5)
+    p = 6
+    M = oracle.multipoles(b, p)
+    s = np.array([0.1, -0.05, 0.2])
+    shifted = oracle.Binned(b.cpd, b.box, b.order, b.cell, b.xq.astype(np.float64) + s, b.offsets, b.counts)
+    Ms = oracle.multipoles(shifted, p)
+    terms = oracle.multipole_terms(p)
+    index = {t: i for i, t in enumerate(terms)}
+    c = int(b.cell[0])
+    for t, (a, bb, k) in enumerate(terms):
+        expect = 0.0
+        for i in range(a + 1):
+            for j in range(bb + 1):
+                for l in range(k + 1):
+                    expect += (math.comb(a, i) * math.comb(bb, j) * math.comb(k, l) * s[0] ** (a - i) *
+                               s[1] ** (bb - j) * s[2] ** (k - l) * M[c, index[(i, j, l)]])
+        assert Ms[c, t] == pytest.approx(expect, rel=1e-10, abs=1e-12)
+
+
+def test_multipoles_of_a_symmetric_cell_have_no_odd_terms():
+    rng = np.random.default_rng(18)
+    h = rng.uniform(-0.2, 0.2, (50, 3))
+    X = (np.concatenate([h, -h]) + 2.5) / 5.0                 # centre of cell (2, 2, 2), point-symmetric
+    b = oracle.bin_positions(X, 5)
+    M = oracle.multipoles(b, 8)
+    c = int(b.cell[0])
+    for t, (a, bb, k) in enumerate(oracle.multipole_terms(8)):
+        if (a + bb + k) % 2:
+            assert abs(M[c, t]) < 1e-15
+    assert M[c, 0] == 100.0
