@@ -61,7 +61,6 @@ struct nf_box {
     // plan: class-ordered items, then the same list with long items split into source pieces
     Item *items_raw = nullptr, *items = nullptr;
     int *n_raw = nullptr, *n_items = nullptr, *queue = nullptr, *err = nullptr;
-    int *class_end_raw = nullptr, *class_end = nullptr;   // 8 ints each
     Piece *pieces = nullptr;
     Reduce *reduces = nullptr;
     int *n_reduce = nullptr;
@@ -296,11 +295,9 @@ int upload_box(nf_t *nf, float4 *acc_out, double *acc64, const float4 *cot)
 int plan(nf_t *nf)
 {
     NF_CK(nf::zero_device_int(nf->n_raw, nf->stream));
-    for (int cls = 0; cls < nf::kClasses; ++cls) {
+    for (int cls = 0; cls < nf::kClasses; ++cls)
         NF_CK(nf::plan_items_class(nf->cell_start, nf->ncell, 0, cls, nf->items_raw, nf->n_raw, nf->counts,
                                    nf->offsets, nf->scan_tmp, nf->stream));
-        NF_CK(nf::copy_device_int(nf->class_end_raw + cls, nf->n_raw, nf->stream));
-    }
     // neighbourhood sizes (left in offsets) and the pass's pair count, then the source split
     NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->pairs, nf->counts, nf->offsets, nf->stream));
     if (nf->h_nbr != nf->offsets) {   // offsets and cell_start trade buffers in nf_set_particles
@@ -310,7 +307,6 @@ int plan(nf_t *nf)
     NF_CK(nf::split_items(nf->items_raw, nf->n_raw, static_cast<int>(nf->item_cap), nf->nbr_ptr, nf->pairs, nf->wf,
                           kSplitFloor, nf->split_k, nf->split_p, nf->split_r, nf->split_scan, nf->items,
                           nf->n_items, nf->pieces, nf->reduces, nf->n_reduce, nf->stream));
-    NF_CK(nf::map_class_ends(nf->split_k, nf->class_end_raw, nf->class_end, nf->stream));
     return NF_OK;
 }
 
@@ -341,10 +337,9 @@ int read_err(nf_t *nf, int *host)
     return NF_OK;
 }
 
-int launch_forces(nf_t *nf, const BoxDev *d_boxes, const Item *items, const int *n_items, const int *class_end,
-                  int *queue, int adjoint)
+int launch_forces(nf_t *nf, const BoxDev *d_boxes, const Item *items, const int *n_items, int *queue, int adjoint)
 {
-    NF_CK(cudaMemsetAsync(queue, 0, 3 * sizeof(int), nf->stream));
+    NF_CK(cudaMemsetAsync(queue, 0, sizeof(int), nf->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (nf->profile) {
         while (nf->ev.size() < nf->ev_used + 2) {
@@ -357,8 +352,7 @@ int launch_forces(nf_t *nf, const BoxDev *d_boxes, const Item *items, const int 
         nf->ev_used += 2;
         NF_CK(cudaEventRecord(e0, nf->stream));
     }
-    NF_CK(nf::launch_pair(d_boxes, items, n_items, class_end, queue, nf->acc_mode == NF_ACC_COMPENSATED, adjoint,
-                          nf->softening,
+    NF_CK(nf::launch_pair(d_boxes, items, n_items, queue, nf->acc_mode == NF_ACC_COMPENSATED, adjoint, nf->softening,
                           nf->shape,
                           nf->sm_count, nf->stream));
     if (nf->profile) NF_CK(cudaEventRecord(e1, nf->stream));
@@ -461,7 +455,6 @@ int nf_create(int cpd, int R, double eps, double box, nf_t **out)
         (rc = dalloc(nf, &nf->n_items, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->queue, sizeof(int) * 4)) ||
         (rc = dalloc(nf, &nf->n_raw, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->n_reduce, sizeof(int) * 4)) ||
         (rc = dalloc(nf, &nf->nbr_ptr, sizeof(int *))) ||
-        (rc = dalloc(nf, &nf->class_end_raw, sizeof(int) * 8)) || (rc = dalloc(nf, &nf->class_end, sizeof(int) * 8)) ||
         (rc = dalloc(nf, &nf->dt_tmp, nf::dt_temp_bytes(nf->ncell))) ||
         (rc = dalloc(nf, &nf->err, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->pairs, sizeof(unsigned long long))) ||
         (rc = dalloc(nf, &nf->d_box, sizeof(BoxDev)))) {
@@ -494,7 +487,7 @@ void nf_destroy(nf_t *nf)
     dfree(nf->cell_start); dfree(nf->counts); dfree(nf->offsets);
     if (nf->scan_tmp) cudaFree(nf->scan_tmp);
     dfree(nf->n_items); dfree(nf->queue); dfree(nf->err); dfree(nf->pairs); dfree(nf->d_box);
-    dfree(nf->n_raw); dfree(nf->n_reduce); dfree(nf->nbr_ptr); dfree(nf->class_end_raw); dfree(nf->class_end);
+    dfree(nf->n_raw); dfree(nf->n_reduce); dfree(nf->nbr_ptr);
     if (nf->dt_tmp) cudaFree(nf->dt_tmp);
     if (nf->stage.p) cudaFree(nf->stage.p);
     for (cudaEvent_t e : nf->ev) cudaEventDestroy(e);
@@ -705,7 +698,7 @@ int nf_forces(nf_t *nf, float *acc)
     }
     if ((rc = upload_box(nf, out, nf->acc64, nullptr))) return rc;
     if (nf->n > 0) {
-        if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->class_end, nf->queue, 0))) return rc;
+        if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
         NF_CK(nf::reduce_partials(nf->d_box, nf->reduces, nf->n_reduce, nf->reduce_cap, 0, nf->stream));
     }
     if (copy_back) NF_CK(cudaMemcpyAsync(acc, nf->acc32, bytes, cudaMemcpyDefault, nf->stream));
@@ -751,7 +744,7 @@ int nf_vjp(nf_t *nf, const float *w, float *grad)
         copy_back = true;
     }
     if ((rc = upload_box(nf, out, nullptr, cot))) return rc;
-    if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->class_end, nf->queue, 1))) return rc;
+    if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 1))) return rc;
     NF_CK(nf::reduce_partials(nf->d_box, nf->reduces, nf->n_reduce, nf->reduce_cap, 1, nf->stream));
     if (copy_back) NF_CK(cudaMemcpyAsync(grad, nf->acc32, bytes, cudaMemcpyDefault, nf->stream));
     return NF_OK;
@@ -895,10 +888,10 @@ int nf_tune(nf_t *nf, char *report, int report_len)
         for (const PairShape &s : cand) {
             if (nf::pair_max_blocks_per_sm(nf->acc_mode == NF_ACC_COMPENSATED, 0, nf->softening, s) < 1) continue;
             nf->shape = s;
-            if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->class_end, nf->queue, 0))) return rc;
+            if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
             NF_CK(cudaEventRecord(a, nf->stream));
             for (int r = 0; r < 2; ++r)
-                if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->class_end, nf->queue, 0))) return rc;
+                if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
             NF_CK(cudaEventRecord(b, nf->stream));
             NF_CK(cudaEventSynchronize(b));
             float t = 0;
@@ -952,7 +945,6 @@ struct Batch {
     int64_t raw_cap = 0, n_cap = 0;
     int nbox_cap = 0, reduce_cap = 0;
     int *n_raw = nullptr, *n_items = nullptr, *n_reduce = nullptr, *queue = nullptr;
-    int *class_end_raw = nullptr, *class_end = nullptr;
     int device = -1;
 };
 
@@ -977,8 +969,7 @@ namespace {
 void batch_release(Batch &b)
 {
     void *ps[] = {b.d_desc, b.items_raw, b.items, b.pieces, b.reduces, b.partials, b.split_k, b.split_p,
-                  b.split_r, b.split_scan, b.nbr_ptrs, b.pair_ptrs, b.total, b.n_raw, b.n_items, b.n_reduce, b.queue,
-                  b.class_end_raw, b.class_end};
+                  b.split_r, b.split_scan, b.nbr_ptrs, b.pair_ptrs, b.total, b.n_raw, b.n_items, b.n_reduce, b.queue};
     for (void *q : ps)
         if (q) cudaFree(q);
     b = Batch();
@@ -1004,8 +995,7 @@ int batch_alloc(nf_t *nf, Batch &B, int nbox, int64_t raw_cap, int64_t n_total)
         (rc = dalloc(nf, &B.pair_ptrs, sizeof(unsigned long long *) * nbox)) ||
         (rc = dalloc(nf, &B.total, sizeof(unsigned long long))) || (rc = dalloc(nf, &B.n_raw, sizeof(int) * 4)) ||
         (rc = dalloc(nf, &B.n_items, sizeof(int) * 4)) || (rc = dalloc(nf, &B.n_reduce, sizeof(int) * 4)) ||
-        (rc = dalloc(nf, &B.queue, sizeof(int) * 4)) || (rc = dalloc(nf, &B.class_end_raw, sizeof(int) * 8)) ||
-        (rc = dalloc(nf, &B.class_end, sizeof(int) * 8))) {
+        (rc = dalloc(nf, &B.queue, sizeof(int) * 4))) {
         batch_release(B);
         return rc;
     }
@@ -1047,12 +1037,10 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
             if ((rc = batch_alloc(nf, B, nbox, raw_cap, n_total))) return rc;
         }
         NF_CK(nf::zero_device_int(B.n_raw, nf->stream));
-        for (int cls = 0; cls < nf::kClasses; ++cls) {
+        for (int cls = 0; cls < nf::kClasses; ++cls)
             for (int b = 0; b < nbox; ++b)
                 NF_CK(nf::plan_items_class(boxes[b]->cell_start, boxes[b]->ncell, b, cls, B.items_raw, B.n_raw,
                                            boxes[b]->counts, boxes[b]->offsets, boxes[b]->scan_tmp, nf->stream));
-            NF_CK(nf::copy_device_int(B.class_end_raw + cls, B.n_raw, nf->stream));
-        }
         std::vector<const int *> nbr(nbox);
         std::vector<const unsigned long long *> prs(nbox);
         for (int b = 0; b < nbox; ++b) {
@@ -1067,7 +1055,6 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
         NF_CK(nf::split_items(B.items_raw, B.n_raw, static_cast<int>(B.raw_cap), B.nbr_ptrs, B.total, nf->wf,
                               kSplitFloor, B.split_k, B.split_p, B.split_r, B.split_scan, B.items, B.n_items, B.pieces,
                               B.reduces, B.n_reduce, nf->stream));
-        NF_CK(nf::map_class_ends(B.split_k, B.class_end_raw, B.class_end, nf->stream));
         NF_CK(cudaStreamSynchronize(nf->stream));   // the host vectors above must outlive their copies
         B.boxes.assign(boxes, boxes + nbox);
         B.gens.resize(nbox);
@@ -1102,7 +1089,7 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
     }
     if (dirty)
         NF_CK(cudaMemcpyAsync(B.d_desc, B.h_desc.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice, nf->stream));
-    if ((rc = launch_forces(nf, B.d_desc, B.items, B.n_items, B.class_end, B.queue, 0))) return rc;
+    if ((rc = launch_forces(nf, B.d_desc, B.items, B.n_items, B.queue, 0))) return rc;
     NF_CK(nf::reduce_partials(B.d_desc, B.reduces, B.n_reduce, B.reduce_cap, 0, nf->stream));
     for (int b = 0; b < nbox; ++b) {
         boxes[b]->have_forces = true;

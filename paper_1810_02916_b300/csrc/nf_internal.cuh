@@ -74,10 +74,8 @@ struct PairShape {
 
 // ---- pair kernel (nf_pair.cu) ----
 // softening: 0 = compact spline (Section 4.3.1), 1 = Plummer (Eq. eqn:plummer)
-// class_end (may be null): end index of each occupancy class in the item
-// list (5 ints); queue: 3 counters, zeroed before each launch.
-cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, const int *class_end, int *queue,
-                        int compensated, int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st);
+cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, int compensated,
+                        int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st);
 int pair_max_blocks_per_sm(int compensated, int adjoint, int softening, PairShape shape);
 
 // ---- scan / sort / binning (nf_sort.cu) ----
@@ -102,10 +100,6 @@ cudaError_t count_keys(const uint32_t *keys, int n, int *counts, cudaStream_t st
 cudaError_t plan_items_class(const int *cell_start, int ncell, int box_index, int cls, Item *items, int *n_items,
                              int *scratch_counts, int *scratch_offsets, void *scan_temp, cudaStream_t st);
 cudaError_t zero_device_int(int *p, cudaStream_t st);
-// dst[i] = *src (records the running item count as the end of a class)
-cudaError_t copy_device_int(int *dst, const int *src, cudaStream_t st);
-// class ends after splitting: dst[c] = k_scan[src[c]] for the 5 classes
-cudaError_t map_class_ends(const int *k_scan, const int *src, int *dst, cudaStream_t st);
 // Split items whose neighbourhood is long against the whole pass into source
 // pieces (see nf_plan.cu).  items_in/n_in: the class-ordered list; nbr[box]:
 // sources in each cell's neighbourhood of that box; total_pairs: pair count of the pass; warps_x_f:

@@ -38,8 +38,8 @@ constexpr size_t kOffItems = align256(kOffDesc + sizeof(nf::BoxDev));
 constexpr size_t kOffCounts = align256(kOffItems + sizeof(nf::Item) * static_cast<size_t>(kMaxItems));
 constexpr size_t kOffOffsets = align256(kOffCounts + sizeof(int) * kCellInts);
 constexpr size_t kOffScan = align256(kOffOffsets + sizeof(int) * kCellInts);
-constexpr size_t kOffWords = align256(kOffScan + sizeof(int) * kScanInts);   // item count, flag, queues, class ends
-constexpr size_t kScratchBytes = align256(kOffWords + 16 * sizeof(int));
+constexpr size_t kOffWords = align256(kOffScan + sizeof(int) * kScanInts);   // n_items, queue, error flag
+constexpr size_t kScratchBytes = align256(kOffWords + 4 * sizeof(int));
 
 static_assert(kScratchBytes == 8390400, "the documented scratch size is out of date");
 
@@ -124,7 +124,7 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     int *offsets = reinterpret_cast<int *>(base + kOffOffsets);
     void *scan_tmp = base + kOffScan;
     int *words = reinterpret_cast<int *>(base + kOffWords);
-    int *n_items = words, *bad = words + 1, *queue = words + 4, *class_end = words + 8;
+    int *n_items = words, *queue = words + 1, *bad = words + 2;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int ncell = cpd * cpd * cpd;
 
@@ -149,10 +149,8 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
 
     // work list (items ordered largest cells first), then the descriptor, then the pair kernel
     NA_CK(nf::zero_device_int(n_items, st));
-    for (int cls = 0; cls < nf::kClasses; ++cls) {
+    for (int cls = 0; cls < nf::kClasses; ++cls)
         NA_CK(nf::plan_items_class(cell_start, ncell, 0, cls, items, n_items, counts, offsets, scan_tmp, st));
-        NA_CK(nf::copy_device_int(class_end + cls, n_items, st));
-    }
     const double inv_w = static_cast<double>(cpd) / box;
     const double ec = eps * inv_w;
     nf::BoxDev d{};
@@ -171,10 +169,10 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     d.grad_scale = inv_w * inv_w * inv_w;
     write_desc<<<1, 1, 0, st>>>(desc, d);
     NA_CK(cudaGetLastError());
-    NA_CK(cudaMemsetAsync(queue, 0, 3 * sizeof(int), st));
+    NA_CK(cudaMemsetAsync(queue, 0, sizeof(int), st));
     int sms = 0;
     NA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    NA_CK(nf::launch_pair(desc, items, n_items, class_end, queue, 1, 0, 0, nf::PairShape{8, 128, 0}, sms, st));
+    NA_CK(nf::launch_pair(desc, items, n_items, queue, 1, 0, 0, nf::PairShape{8, 128, 0}, sms, st));
 #undef NA_CK
     return NF_OK;
 }

@@ -47,12 +47,6 @@ namespace {
 #ifndef NF_STAGE_A
 #define NF_STAGE_A 128   // sources staged per round for the launch shape's stage = 128
 #endif
-#ifndef NF_FETCH_G1
-#define NF_FETCH_G1 4    // items per queue grab, cells of 8..63 particles
-#endif
-#ifndef NF_FETCH_G2
-#define NF_FETCH_G2 32   // items per queue grab, cells of 1..7 particles
-#endif
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
@@ -505,7 +499,6 @@ template <int B, bool COMP, bool ADJ, int SOFT>
 __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *__restrict__ boxes,
                                                                   const Item *__restrict__ items,
                                                                   const int *__restrict__ n_items_p,
-                                                                  const int *__restrict__ class_end,
                                                                   int *__restrict__ queue)
 {
     extern __shared__ __align__(16) float4 smem_f4[];
@@ -517,38 +510,12 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
     int *tabs = reinterpret_cast<int *>(w0 + (ADJ ? 4 : 2) * B + (COMP ? 192 : 0));
     int *tstart = tabs, *tpre = tabs + 128;
     unsigned char *tslot = reinterpret_cast<unsigned char *>(tabs + 256);
-    // Three queues over the class-ordered list: items of cells with >= 64
-    // particles one at a time (longest first), then cells of 8..63 in grabs
-    // of NF_FETCH_G1, then cells of < 8 in grabs of NF_FETCH_G2 -- one atomic
-    // per grab instead of one per (short) item.
     const int n_items = *n_items_p;
-    const int e0 = class_end ? min(class_end[2], n_items) : n_items;
-    const int e1 = class_end ? min(class_end[3], n_items) : n_items;
-    int region = 0, it = 0, end = 0;
     for (;;) {
-        if (it >= end) {
-            int b = 0, e = 0;
-            if (lane == 0) {
-                while (region < 3) {
-                    if (region == 0) {
-                        b = atomicAdd(&queue[0], 1);
-                        e = min(b + 1, e0);
-                    } else if (region == 1) {
-                        b = e0 + atomicAdd(&queue[1], NF_FETCH_G1);
-                        e = min(b + NF_FETCH_G1, e1);
-                    } else {
-                        b = e1 + atomicAdd(&queue[2], NF_FETCH_G2);
-                        e = min(b + NF_FETCH_G2, n_items);
-                    }
-                    if (b < e) break;
-                    ++region;
-                }
-            }
-            region = __shfl_sync(kFull, region, 0);
-            if (region >= 3) break;
-            it = __shfl_sync(kFull, b, 0);
-            end = __shfl_sync(kFull, e, 0);
-        }
+        int it = 0;
+        if (lane == 0) it = atomicAdd(queue, 1);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_items) break;
         const Item item = items[it];
         const BoxDev &bx = boxes[item_box(item)];
         const int cnt = item_count(item);
@@ -561,7 +528,6 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
         else
             run_item<4, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         __syncwarp();
-        ++it;
     }
 }
 
@@ -601,15 +567,14 @@ int blocks_per_sm(int warps)
 }
 
 template <int B, bool COMP, bool ADJ, int SOFT>
-cudaError_t launch_t(const BoxDev *boxes, const Item *items, const int *n_items, const int *class_end, int *queue,
-                     PairShape shape, int sm_count, cudaStream_t st)
+cudaError_t launch_t(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, PairShape shape,
+                     int sm_count, cudaStream_t st)
 {
     const int per_sm = blocks_per_sm<B, COMP, ADJ, SOFT>(shape.warps);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int blocks = shape.blocks > 0 ? shape.blocks : sm_count * per_sm;
     pair_kernel<B, COMP, ADJ, SOFT><<<blocks, shape.warps * 32, smem_bytes<B, COMP, ADJ>(shape.warps), st>>>(boxes, items,
-                                                                                                      n_items, class_end,
-                                                                                                      queue);
+                                                                                                      n_items, queue);
     return cudaGetLastError();
 }
 
@@ -641,11 +606,11 @@ int max_blocks_t(PairShape shape)
         NF_PAIR_DISPATCH_S(FN, 0, __VA_ARGS__);                                                                     \
     } while (0)
 
-cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, const int *class_end, int *queue,
-                        int compensated, int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st)
+cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, int compensated,
+                        int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st)
 {
     if (shape.warps < 1 || shape.warps > 8 || (shape.stage != 128 && shape.stage != 256)) return cudaErrorInvalidValue;
-    NF_PAIR_DISPATCH(launch_t, boxes, items, n_items, class_end, queue, shape, sm_count, st);
+    NF_PAIR_DISPATCH(launch_t, boxes, items, n_items, queue, shape, sm_count, st);
 }
 
 int pair_max_blocks_per_sm(int compensated, int adjoint, int softening, PairShape shape)

@@ -285,26 +285,6 @@ cudaError_t reduce_partials(const BoxDev *boxes, const Reduce *reduces, const in
     return cudaGetLastError();
 }
 
-__global__ void copy_int_kernel(int *dst, const int *src) { *dst = *src; }
-
-__global__ void map_ends_kernel(const int *k_scan, const int *src, int *dst)
-{
-    const int c = threadIdx.x;
-    if (c < kClasses) dst[c] = k_scan[src[c]];
-}
-
-cudaError_t copy_device_int(int *dst, const int *src, cudaStream_t st)
-{
-    copy_int_kernel<<<1, 1, 0, st>>>(dst, src);
-    return cudaGetLastError();
-}
-
-cudaError_t map_class_ends(const int *k_scan, const int *src, int *dst, cudaStream_t st)
-{
-    map_ends_kernel<<<1, 32, 0, st>>>(k_scan, src, dst);
-    return cudaGetLastError();
-}
-
 cudaError_t zero_device_int(int *p, cudaStream_t st)
 {
     zero_int<<<1, 1, 0, st>>>(p);
