@@ -338,47 +338,7 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
         src_lo = __ldg(&bx.pieces[item.piece].src_lo);
         src_hi = min(__ldg(&bx.pieces[item.piece].src_hi), total);
     }
-    // Small sparse neighbourhoods (split mode, <= 2B sources, no cell above 16
-    // particles): each lane copies its own four table cells straight into the
-    // stage buffer with the cell shift applied -- no search, one round.
-    bool direct = false;
-    if (SPLIT && item.piece < 0 && total <= 2 * B) {
-        int mc = 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int t = 4 * lane + u;
-            if (t < kNbr) mc = max(mc, tpre[t + 1] - tpre[t]);
-        }
-        direct = __reduce_max_sync(kFull, mc) <= 16;
-    }
-    if (direct) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int t = 4 * lane + u;
-            if (t < kNbr) {
-                const int s0 = tstart[t], cnt = tpre[t + 1] - tpre[t], dst = tpre[t];
-                const float sx = static_cast<float>(t / 25 - 2), sy = static_cast<float>((t / 5) % 5 - 2),
-                            sz = static_cast<float>(t % 5 - 2);
-                for (int i = 0; i < cnt; ++i) {
-                    float4 q = __ldg(bx.pos + s0 + i);
-                    q.x += sx; q.y += sy; q.z += sz;
-                    stage[dst + i] = q;
-                    if (ADJ) wstage[dst + i] = __ldg(bx.cot + s0 + i);
-                }
-            }
-        }
-        __syncwarp();
-        for (int j = my_split; j < total; j += splits) {
-            if (ADJ)
-                pair_adjoint<SOFT>(stage[j], wstage[j], xi[0], yi[0], zi[0], wx[0], wy[0], wz[0], px[0], py[0], pz[0],
-                                   a0, a1, a2, eps2);
-            else
-                pair_force<SOFT>(stage[j], xi[0], yi[0], zi[0], px[0], py[0], pz[0], a0, a1, a2, eps2);
-        }
-        if (COMP) comp_fold_smem(comp + lane, px[0], py[0], pz[0]);
-        __syncwarp();
-    }
-    const int rounds = (!direct && src_hi > src_lo) ? (src_hi - src_lo + B - 1) / B : 0;
+    const int rounds = src_hi > src_lo ? (src_hi - src_lo + B - 1) / B : 0;
 
     if (rounds > 0) stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, src_lo, src_hi, lane, tslot);
     for (int r = 0; r < rounds; ++r) {
