@@ -294,3 +294,25 @@ def test_plummer_adjoint_matches_oracle():
     ref = oracle.vjp(b, w.eps / 2.16, W[:, :3].astype(np.float64), sinks, soft=oracle.PLUMMER)
     s = oracle.error_stats(g[sinks, :3], ref)
     assert s["rms_rel"] <= 1e-5, s
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["compensated", "plain"])
+def test_sparse_cells_direct_staging(mode):
+    """About one particle per cell: neighbourhoods of <= 256 sources staged in one direct copy."""
+    rng = np.random.default_rng(32)
+    cpd = 25
+    X = rng.random((20000, 3))
+    X[:40] = X[0] + 0.001 * rng.standard_normal((40, 3))          # one crowded cell keeps the general path busy
+    X = np.mod(X, 1.0)
+    eps = 0.02 / cpd
+    nf = make_box(X, cpd, eps, mode=mode)
+    b = oracle_side(X, cpd)
+    acc = nf.forces()
+    ref, sa, _ = oracle.forces(b, eps, with_sumabs=True)
+    _check_forces(acc, ref, sa, tol=RMS_TOL if mode == 0 else RMS_TOL_PLAIN)
+    W = np.zeros((nf.n, 4), np.float32)
+    W[:, :3] = gen.cotangent(nf.n, rng).astype(np.float32)
+    g = nf.vjp(W)
+    gref = oracle.vjp(b, eps, W[:, :3].astype(np.float64))
+    s = oracle.error_stats(g[:, :3], gref)
+    assert s["rms_rel"] <= 1e-5, s
