@@ -23,8 +23,11 @@
 //     <= 16 sinks the lanes split the sources between them (each sink owns
 //     32/P lanes, P = sinks rounded up to a power of two) and the partial
 //     sums are combined with a fixed xor-shuffle tree;
-//   * pair arithmetic is FP32: rsqrt on the SFU plus one Newton step, 20 FP32
-//     pipe operations per pair;
+//   * pair arithmetic is FP32: rsqrt on the SFU plus one Newton step: 18 FP32
+//     FMA-pipe operations, one min and one SFU op per pair; lanes holding 2 or
+//     4 sinks evaluate two sinks per paired FP32 instruction (FADD2 / FMUL2 /
+//     FFMA2), which halves the issue slots so the FP32 lanes, not instruction
+//     issue, bound the loop;
 //   * accumulation: plain FFMA within a round (<= B sources), folded after
 //     every round into a (hi, lo) pair with an exact two-sum and reduced to
 //     FP64 per sink at the end (compensated mode); or one FP32 running sum
@@ -42,7 +45,10 @@ namespace nf {
 namespace {
 
 #ifndef NF_SRC_UNROLL
-#define NF_SRC_UNROLL 8   // staged sources evaluated per unrolled step of the broadcast loop
+#define NF_SRC_UNROLL 4   // staged sources evaluated per unrolled step of the broadcast loop
+#endif
+#ifndef NF_PACKED
+#define NF_PACKED 1   // paired FP32 instructions for two sinks when a lane holds 2 or 4 sinks
 #endif
 #ifndef NF_STAGE_A
 #define NF_STAGE_A 128   // sources staged per round for the launch shape's stage = 128
@@ -76,17 +82,6 @@ struct Comp3 {
     float hx, hy, hz;   // running high parts
     float lx, ly, lz;   // accumulated low parts
 };
-
-__device__ __forceinline__ void comp_init(Comp3 &c) { c.hx = c.hy = c.hz = c.lx = c.ly = c.lz = 0.f; }
-
-__device__ __forceinline__ void comp_fold(Comp3 &c, float &px, float &py, float &pz)
-{
-    float s, e;
-    two_sum(c.hx, px, s, e); c.hx = s; c.lx = __fadd_rn(c.lx, e);
-    two_sum(c.hy, py, s, e); c.hy = s; c.ly = __fadd_rn(c.ly, e);
-    two_sum(c.hz, pz, s, e); c.hz = s; c.lz = __fadd_rn(c.lz, e);
-    px = py = pz = 0.f;
-}
 
 // combine with the partner lane `o` (xor); both lanes end with the same value
 __device__ __forceinline__ void comp_xor_combine(Comp3 &c, int o)
@@ -136,6 +131,47 @@ __device__ __forceinline__ void pair_force(const float4 q, float xi, float yi, f
     ax = fmaf(f, dx, ax);
     ay = fmaf(f, dy, ay);
     az = fmaf(f, dz, az);
+}
+
+// Two sinks against one source with Blackwell's paired FP32 instructions
+// (FADD2 / FMUL2 / FFMA2: one issue slot for two lanes' worth of FP32 work).
+// Every lane of a pair follows exactly the scalar pair_force arithmetic
+// (round-to-nearest each op, same order), so results are bit-identical.
+// nx, ny, nz hold minus the two sinks' offsets.
+template <int SOFT>
+__device__ __forceinline__ void pair_force2(const float2 qx, const float2 qy, const float2 qz, const float2 nx,
+                                            const float2 ny, const float2 nz, float2 &ax, float2 &ay, float2 &az,
+                                            const float2 a0, const float2 a1, const float2 a2, const float2 eps2)
+{
+    const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
+    const float2 half = make_float2(0.5f, 0.5f), mhalf = make_float2(-0.5f, -0.5f);
+    if (SOFT == 1) {
+        const float2 s2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
+        float2 y = make_float2(rsqrtf(s2.x), rsqrtf(s2.y));
+        const float2 t = __fmul2_rn(s2, y);
+        const float2 h = __fmul2_rn(t, y);
+        const float2 e = __ffma2_rn(h, mhalf, half);
+        y = __ffma2_rn(y, e, y);
+        const float2 f = __fmul2_rn(__fmul2_rn(y, y), y);
+        ax = __ffma2_rn(f, dx, ax);
+        ay = __ffma2_rn(f, dy, ay);
+        az = __ffma2_rn(f, dz, az);
+        return;
+    }
+    const float2 fmin2 = make_float2(FLT_MIN, FLT_MIN);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, fmin2)));
+    float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 t = __fmul2_rn(r2, y);
+    const float2 h = __fmul2_rn(t, y);
+    const float2 e = __ffma2_rn(h, mhalf, half);
+    y = __ffma2_rn(y, e, y);
+    const float2 r = __ffma2_rn(t, e, t);
+    const float2 y3 = __fmul2_rn(__fmul2_rn(y, y), y);
+    const float2 g = __ffma2_rn(__ffma2_rn(a2, r, a1), r, a0);
+    const float2 f = make_float2(fminf(y3.x, g.x), fminf(y3.y, g.y));
+    ax = __ffma2_rn(f, dx, ax);
+    ay = __ffma2_rn(f, dy, ay);
+    az = __ffma2_rn(f, dz, az);
 }
 
 // one pair of the adjoint: grad += J(d) (w_j - w_k), J = f I + (f'/r) d d^T
@@ -330,6 +366,20 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
         }
     }
     const float a0 = bx.a0, a1 = bx.a1, a2 = bx.a2, eps2 = bx.eps2;
+    constexpr bool PACK = NF_PACKED && !ADJ && SS >= 2;
+    constexpr int SP = SS >= 2 ? SS / 2 : 1;
+    float2 nx2[SP], ny2[SP], nz2[SP], ax2[SP], ay2[SP], az2[SP];
+    if (PACK) {
+#pragma unroll
+        for (int k = 0; k < SP; ++k) {
+            nx2[k] = make_float2(-xi[2 * k], -xi[2 * k + 1]);
+            ny2[k] = make_float2(-yi[2 * k], -yi[2 * k + 1]);
+            nz2[k] = make_float2(-zi[2 * k], -zi[2 * k + 1]);
+            ax2[k] = ay2[k] = az2[k] = make_float2(0.f, 0.f);
+        }
+    }
+    const float2 a02 = make_float2(a0, a0), a12 = make_float2(a1, a1), a22 = make_float2(a2, a2),
+                 e22 = make_float2(eps2, eps2);
 
     const int total = build_table(bx, item.cell, tstart, tpre, lane);
     // the whole flattened neighbourhood, or this item's piece of it
@@ -369,7 +419,14 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const float4 q = buf[j + u];
-                    if (ADJ) {
+                    if (PACK) {
+                        const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
+                                     qz = make_float2(q.z, q.z);
+#pragma unroll
+                        for (int k = 0; k < SP; ++k)
+                            pair_force2<SOFT>(qx, qy, qz, nx2[k], ny2[k], nz2[k], ax2[k], ay2[k], az2[k], a02, a12,
+                                              a22, e22);
+                    } else if (ADJ) {
                         const float4 wq = wbuf[j + u];
 #pragma unroll
                         for (int s = 0; s < SS; ++s)
@@ -384,10 +441,25 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
             }
         }
         if (COMP) {
+            if (PACK) {
 #pragma unroll
-            for (int s = 0; s < SS; ++s) comp_fold_smem(comp + lane + 32 * s, px[s], py[s], pz[s]);
+                for (int k = 0; k < SP; ++k) {
+                    comp_fold_smem(comp + lane + 32 * (2 * k), ax2[k].x, ay2[k].x, az2[k].x);
+                    comp_fold_smem(comp + lane + 32 * (2 * k + 1), ax2[k].y, ay2[k].y, az2[k].y);
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < SS; ++s) comp_fold_smem(comp + lane + 32 * s, px[s], py[s], pz[s]);
+            }
         }
         __syncwarp();
+    }
+    if (PACK && !COMP) {
+#pragma unroll
+        for (int k = 0; k < SP; ++k) {
+            px[2 * k] = ax2[k].x; py[2 * k] = ay2[k].x; pz[2 * k] = az2[k].x;
+            px[2 * k + 1] = ax2[k].y; py[2 * k + 1] = ay2[k].y; pz[2 * k + 1] = az2[k].y;
+        }
     }
     Comp3 acc[SS];
 #pragma unroll
