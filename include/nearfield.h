@@ -253,7 +253,9 @@ int nf_profile_read(nf_t *nf, int64_t *launches, double *ms);
  * nf_set_shape / nf_tune -- launch shape of the pair kernel: warps per block
  * (1..8) and sources staged per round (128 or 256).  nf_tune times every
  * candidate on this machine's particles (a few pair passes), keeps the fastest
- * and caches it per device and occupancy signature for later boxes;
+ * and caches it per device and occupancy signature for later boxes (in
+ * memory, and in the text file named by the NF_TUNE_CACHE environment
+ * variable when it is set, so later processes reuse it);
  * report (may be NULL) receives a one-line summary.  Synchronises.
  */
 int nf_set_shape(nf_t *nf, int warps, int stage);

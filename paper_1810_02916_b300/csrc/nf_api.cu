@@ -401,6 +401,39 @@ int produce_out(nf_t *nf, void *dst, size_t bytes, F produce)
 
 std::mutex g_tune_mu;
 std::map<std::string, PairShape> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+// Tuning results persist across processes in the text file named by
+// NF_TUNE_CACHE (one "key<TAB>warps<TAB>stage" line per entry), if set.
+void tune_file_load()
+{
+    if (g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    const char *path = std::getenv("NF_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        char *t1 = std::strchr(line, '\t');
+        if (!t1) continue;
+        *t1 = 0;
+        int w = 0, b = 0;
+        if (std::sscanf(t1 + 1, "%d\t%d", &w, &b) == 2 && w >= 1 && w <= 8 && (b == 128 || b == 256))
+            g_tune_cache[line] = PairShape{w, b, 0};
+    }
+    std::fclose(f);
+}
+
+void tune_file_append(const std::string &key, PairShape sh)
+{
+    const char *path = std::getenv("NF_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s\t%d\t%d\n", key.c_str(), sh.warps, sh.stage);
+    std::fclose(f);
+}
 
 }  // namespace
 
@@ -869,6 +902,7 @@ int nf_tune(nf_t *nf, char *report, int report_len)
     std::string summary;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_file_load();
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             nf->shape = it->second;
@@ -911,6 +945,7 @@ int nf_tune(nf_t *nf, char *report, int report_len)
         nf->have_forces = true;
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best_s;
+        tune_file_append(key, best_s);
         char part[64];
         std::snprintf(part, sizeof(part), "-> %dx%d", best_s.warps, best_s.stage);
         summary += part;

@@ -2,6 +2,8 @@
 (and its autograd wrapper), the batched persistent launch (also under a
 captured CUDA graph), the launch-shape tuner, and sampled parity at the full
 workload sizes."""
+import os
+
 import numpy as np
 import pytest
 
@@ -275,3 +277,20 @@ def test_cell_multipoles_match_oracle(order):
     tol = 1e-13 * b.counts.astype(np.float64)[:, None] + 1e-12 * np.abs(ref)
     assert np.all(np.abs(M - ref) <= tol)
     assert np.array_equal(M[:, 0], b.counts.astype(np.float64))
+
+
+def test_tuner_result_persists_in_the_cache_file(tmp_path):
+    """A second process reads the tuned shape back from NF_TUNE_CACHE instead of timing again."""
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    code = ("import sys; sys.path.insert(0, %r); import numpy as np; import paper_1810_02916_b300 as nfb; "
+            "nf = nfb.NearField(9, 1e-3); nf.bin_particles(np.random.default_rng(1).random((40000, 3))); "
+            "nf.forces(False); print(nf.tune())") % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))),)
+    env = dict(os.environ, NF_TUNE_CACHE=str(cache))
+    first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert first.returncode == 0, first.stderr
+    assert "->" in first.stdout and cache.exists() and cache.read_text().count("\t") == 2
+    second = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert second.returncode == 0, second.stderr
+    assert second.stdout.strip() == "cached"
