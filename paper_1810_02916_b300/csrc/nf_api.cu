@@ -201,6 +201,9 @@ int ensure_capacity(nf_t *nf, int64_t n)
     // items per cell <= 1 + n_c / 16 (full tiles and remainder pieces of >= 16 sinks, plus one)
     const int64_t item_cap = std::min<int64_t>(n, nf->ncell) + n / 16 + 16;
     if (n <= nf->cap && item_cap <= nf->item_cap && nf->pos) return NF_OK;
+    // item indices and partial-sum slots are 32-bit on the device
+    if (item_cap + 2 * nf->wf + 64 > INT32_MAX || static_cast<int64_t>(nf::kTile) * (2 * nf->wf + 64) + n > INT32_MAX)
+        return fail(nf, NF_EINVAL, "too many particles for one box");
     cudaStreamSynchronize(nf->stream);
     free_particles(nf);
     const int64_t c = n < 1 ? 1 : n;
