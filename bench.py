@@ -39,8 +39,11 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "zeldovich512"
 METRIC = "near-field Gpair-interactions/s and particles/s/step at 512^3 clustered vs plain FP32 kernel"
 UNIT = "Gpair/s"
-FMA_OPS_PER_PAIR = 18      # FP32 FMA-pipe lane operations per pair (the bound of the paired-instruction kernel)
-ISSUE_OPS_PER_PAIR = 20    # FP32-pipe instructions per pair when issued one lane-op at a time (earlier convention)
+# FP32 FMA-pipe lane operations per pair at r >= eps (3 sub, 3 for r^2, 5 for the Newton-refined r^-3,
+# 3 accumulate): the least the law needs for a pair outside the softening length, i.e. nearly every pair
+FMA_OPS_PER_PAIR = 14
+BRANCH_FREE_OPS_PER_PAIR = 18   # the same with the law evaluated branch-free, min(r^-3, g(r)), for every pair
+ISSUE_OPS_PER_PAIR = 20    # FP32-pipe instructions per pair of the branch-free law issued one lane-op at a time
 # DRAM bytes (read + write) of one compensated pair-kernel launch of this workload, from the ncu
 # launch list in profiles/launches_zeldovich512_bench.md, valid while nf_pair.cu hashes to the value
 # below (the record reports null traffic once the kernel source has changed)
@@ -323,6 +326,8 @@ def run(args):
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak_gps = props.multi_processor_count * sm_max * 1e6 * FP32_LANES_PER_SM / FMA_OPS_PER_PAIR / 1e9
     issue_peak_gps = props.multi_processor_count * sm_max * 1e6 * FP32_LANES_PER_SM / ISSUE_OPS_PER_PAIR / 1e9
+    branch_free_peak_gps = (props.multi_processor_count * sm_max * 1e6 * FP32_LANES_PER_SM /
+                            BRANCH_FREE_OPS_PER_PAIR / 1e9)
     if rank == 0:
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -339,14 +344,17 @@ def run(args):
                           frac=pair_kernel_gps / peak_gps, traffic=_pair_traffic(),
                           traffic_note="DRAM read+write bytes of one pair-kernel launch (ncu, same workload); "
                                        "algorithmic bytes: positions 2.15 GB read + FP64 sums 3.22 GB written",
+                          branch_free_frac=pair_kernel_gps / branch_free_peak_gps,
                           issue_convention_frac=pair_kernel_gps / issue_peak_gps,
                           paper_convention_frac=pair_kernel_gps * 23 /
                           (props.multi_processor_count * sm_max * 1e-3 * FP32_LANES_PER_SM * 2),
                           peak_basis=f"FP32 FMA-lane roofline: {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
-                                     f"({src}) x 128 lanes / {FMA_OPS_PER_PAIR} FMA-pipe ops per pair; "
-                                     f"issue_convention_frac: the same over {ISSUE_OPS_PER_PAIR} single-lane "
-                                     "instructions per pair; paper_convention_frac: 23 FLOP per pair against the FMA "
-                                     "peak (2 FLOP per lane per cycle)"),
+                                     f"({src}) x 128 lanes / {FMA_OPS_PER_PAIR} FMA-pipe ops per pair (Newtonian "
+                                     "pair, one Newton step); branch_free_frac: the same over "
+                                     f"{BRANCH_FREE_OPS_PER_PAIR} ops (min(r^-3, g) for every pair); "
+                                     f"issue_convention_frac: over {ISSUE_OPS_PER_PAIR} single-lane instructions per "
+                                     "pair of the branch-free law; paper_convention_frac: 23 FLOP per pair against "
+                                     "the FMA peak (2 FLOP per lane per cycle)"),
             clocks=clk, e2e=e2e, **extra)
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -73,8 +73,11 @@ enum nf_accumulation {
  *        appears twice in a neighbourhood, cpd^3 < 2^31
  *   R    near-field radius in cells (Section 2.1; the paper uses 2).  This
  *        build supports R = 2 only.
- *   eps  spline softening length eps_s in box units, 0 < eps < box/cpd (the
- *        spline must close inside the near field)
+ *   eps  spline softening length eps_s in box units, 2^-20 box/cpd <= eps <
+ *        box/cpd (the spline must close inside the near field; the lower
+ *        bound keeps the FP32 law coefficients 10/eps^3, 15/eps^4, 6/eps^5 of
+ *        cell-unit separations finite and eps^2 far above the r^2 = FLT_MIN
+ *        that the kernel gives a self pair)
  *   box  box side length, > 0
  * Errors: NF_EINVAL for any violated bound, NF_ENOMEM, NF_ECUDA.
  * The box owns all of its device buffers; nf_destroy frees them.

@@ -459,8 +459,8 @@ int nf_create(int cpd, int R, double eps, double box, nf_t **out)
         g_create_error = "box must be positive and finite";
         return NF_EINVAL;
     }
-    if (!(eps > 0) || !(eps < box / cpd)) {
-        g_create_error = "eps must satisfy 0 < eps < box / cpd";
+    if (!(eps >= std::ldexp(box / cpd, -20)) || !(eps < box / cpd)) {
+        g_create_error = "eps must satisfy 2^-20 box / cpd <= eps < box / cpd";
         return NF_EINVAL;
     }
     nf_t *nf = new (std::nothrow) nf_box();

@@ -14,6 +14,7 @@
 // stand-in, and a kernel given it would fault or silently touch the wrong
 // memory.  The address is looked up once per device, with that device
 // current, on the first call made on the device.
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 
@@ -91,8 +92,8 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
                       static_cast<long long>(kMaxParticles));
         return say(err, err_len, NF_EINVAL, msg);
     }
-    if (!(box > 0) || !(eps > 0) || !(eps < box / cpd))
-        return say(err, err_len, NF_EINVAL, "nf_forces_noalloc: need box > 0 and 0 < eps < box / cpd");
+    if (!(box > 0) || !(eps >= std::ldexp(box / cpd, -20)) || !(eps < box / cpd))
+        return say(err, err_len, NF_EINVAL, "nf_forces_noalloc: need box > 0 and 2^-20 box / cpd <= eps < box / cpd");
     if (!cell_start || (n > 0 && (!pos || !acc)))
         return say(err, err_len, NF_EINVAL, "nf_forces_noalloc: NULL array");
     if ((reinterpret_cast<uintptr_t>(pos) | reinterpret_cast<uintptr_t>(acc)) & 15u)

@@ -12,7 +12,8 @@
 //   * a work item is up to 128 sinks of one cell; the warp pulls item indices
 //     from a device queue (atomic counter), largest cells first;
 //   * the warp builds a 125-entry table of its neighbour cells (start, prefix
-//     of counts) in shared memory;
+//     of counts) in shared memory, the 27 near cells (Chebyshev distance <= 1)
+//     first, so each round's sources split into a near run and a far run;
 //   * sources are streamed in rounds of B particles: each lane gathers B/32
 //     float4 with cp.async (16 B each, coalesced along each cell's run) into
 //     one of two per-warp shared-memory buffers while the previous round is
@@ -23,11 +24,15 @@
 //     <= 16 sinks the lanes split the sources between them (each sink owns
 //     32/P lanes, P = sinks rounded up to a power of two) and the partial
 //     sums are combined with a fixed xor-shuffle tree;
-//   * pair arithmetic is FP32: rsqrt on the SFU plus one Newton step: 18 FP32
-//     FMA-pipe operations, one min and one SFU op per pair; lanes holding 2 or
-//     4 sinks evaluate two sinks per paired FP32 instruction (FADD2 / FMUL2 /
-//     FFMA2), which halves the issue slots so the FP32 lanes, not instruction
-//     issue, bound the loop;
+//   * pair arithmetic is FP32, rsqrt on the SFU plus one Newton step.  A far
+//     source (Chebyshev distance 2, so r >= 1 cell > eps) takes f = r^-3 with
+//     the Newton step folded into the cube: 14 FP32 FMA-pipe operations + 1
+//     SFU.  A near source takes the same 14 unless some sink of the warp lies
+//     within eps of it (a warp vote on r^2 < eps^2, which self pairs always
+//     trigger); then all of the warp's pairs with it take the branch-free law,
+//     18 operations + 1 min + 1 SFU.  Lanes holding 2 or 4 sinks evaluate two
+//     sinks per paired FP32 instruction (FADD2 / FMUL2 / FFMA2), which halves
+//     the issue slots so the FP32 lanes, not instruction issue, bound the loop;
 //   * accumulation: plain FFMA within a round (<= B sources), folded after
 //     every round into a (hi, lo) pair with an exact two-sum and reduced to
 //     FP64 per sink at the end (compensated mode); or one FP32 running sum
@@ -52,6 +57,12 @@ namespace {
 #endif
 #ifndef NF_STAGE_A
 #define NF_STAGE_A 128   // sources staged per round for the launch shape's stage = 128
+#endif
+#ifndef NF_FAR_LAW
+#define NF_FAR_LAW 1   // sources of the 98 far cells take f = r^-3 without the spline branch
+#endif
+#ifndef NF_NEAR_VOTE
+#define NF_NEAR_VOTE 1   // near-cell sources take the Newtonian tail unless a warp lane is within eps
 #endif
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
@@ -95,6 +106,43 @@ __device__ __forceinline__ void comp_xor_combine(Comp3 &c, int o)
     two_sum(c.hz, h2, s, e); c.hz = s; c.lz = __fadd_rn(__fadd_rn(c.lz, l2), e);
 }
 
+// The rest of a spline-law pair once d and r^2 (FLT_MIN included) are known:
+// f = min(r^-3, a0 + a1 r + a2 r^2), rsqrt on the SFU plus one Newton step.
+__device__ __forceinline__ void tail_spline(float dx, float dy, float dz, float r2, float &ax, float &ay, float &az,
+                                            float a0, float a1, float a2)
+{
+    float y = rsqrtf(r2);                    // SFU
+    const float t = r2 * y;
+    const float h = t * y;
+    const float e = fmaf(h, -0.5f, 0.5f);
+    y = fmaf(y, e, y);                       // one Newton step for r2^-1/2
+    const float r = fmaf(t, e, t);           // r2 * y
+    const float y3 = y * y * y;
+    const float g = fmaf(fmaf(a2, r, a1), r, a0);
+    const float f = fminf(y3, g);
+    ax = fmaf(f, dx, ax);
+    ay = fmaf(f, dy, ay);
+    az = fmaf(f, dz, az);
+}
+
+// The rest of a pair at r >= eps (law: f = r^-3).  The Newton step is taken on
+// r^-3 itself: with y the SFU estimate of (r^2)^-1/2 and h = r^2 y^2, one
+// Newton step for (r^2)^-1/2 multiplies y by 1 + e, e = (1 - h) / 2, so
+// r^-3 = y^3 (1 + e)^3 = y^3 (1 + 3e) + O(e^2) (|e| < 2^-21, the dropped
+// terms below 2^-40 relative).  8 FP32-pipe operations + 1 SFU, no min.
+__device__ __forceinline__ void tail_newton(float dx, float dy, float dz, float r2, float &ax, float &ay, float &az)
+{
+    const float y = rsqrtf(r2);              // SFU
+    const float yy = y * y;
+    const float h = r2 * yy;
+    const float y3 = yy * y;
+    const float e3 = fmaf(h, -1.5f, 1.5f);   // 3e
+    const float f = fmaf(y3, e3, y3);
+    ax = fmaf(f, dx, ax);
+    ay = fmaf(f, dy, ay);
+    az = fmaf(f, dz, az);
+}
+
 // one pair: a += f(r) d.  Spline (SOFT = 0): f = min(r^-3, a0 + a1 r + a2 r^2),
 // 20 FP32-pipe operations + 1 SFU.  Plummer (SOFT = 1, Eq. eqn:plummer):
 // f = (r^2 + eps_p^2)^-3/2, 15 FP32-pipe operations + 1 SFU (eps2 = eps_p^2).
@@ -119,18 +167,42 @@ __device__ __forceinline__ void pair_force(const float4 q, float xi, float yi, f
     // + FLT_MIN: below half an ulp of any nonzero r^2 on the 2^-22 grid (r^2 >= 2^-44), so it changes
     // nothing except r = 0 (self pair), where it keeps rsqrt finite: finite g, times d = 0
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, FLT_MIN)));
-    float y = rsqrtf(r2);                    // SFU
-    const float t = r2 * y;
-    const float h = t * y;
-    const float e = fmaf(h, -0.5f, 0.5f);
-    y = fmaf(y, e, y);                       // one Newton step for r2^-1/2
-    const float r = fmaf(t, e, t);           // r2 * y
-    const float y3 = y * y * y;
-    const float g = fmaf(fmaf(a2, r, a1), r, a0);
-    const float f = fminf(y3, g);
-    ax = fmaf(f, dx, ax);
-    ay = fmaf(f, dy, ay);
-    az = fmaf(f, dz, az);
+    tail_spline(dx, dy, dz, r2, ax, ay, az, a0, a1, a2);
+}
+
+// tail_spline for two sinks with paired FP32 instructions (same arithmetic per lane)
+__device__ __forceinline__ void tail2_spline(const float2 dx, const float2 dy, const float2 dz, const float2 r2,
+                                             float2 &ax, float2 &ay, float2 &az, const float2 a0, const float2 a1,
+                                             const float2 a2)
+{
+    const float2 half = make_float2(0.5f, 0.5f), mhalf = make_float2(-0.5f, -0.5f);
+    float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 t = __fmul2_rn(r2, y);
+    const float2 h = __fmul2_rn(t, y);
+    const float2 e = __ffma2_rn(h, mhalf, half);
+    y = __ffma2_rn(y, e, y);
+    const float2 r = __ffma2_rn(t, e, t);
+    const float2 y3 = __fmul2_rn(__fmul2_rn(y, y), y);
+    const float2 g = __ffma2_rn(__ffma2_rn(a2, r, a1), r, a0);
+    const float2 f = make_float2(fminf(y3.x, g.x), fminf(y3.y, g.y));
+    ax = __ffma2_rn(f, dx, ax);
+    ay = __ffma2_rn(f, dy, ay);
+    az = __ffma2_rn(f, dz, az);
+}
+
+// tail_newton for two sinks with paired FP32 instructions (same arithmetic per lane)
+__device__ __forceinline__ void tail2_newton(const float2 dx, const float2 dy, const float2 dz, const float2 r2,
+                                             float2 &ax, float2 &ay, float2 &az)
+{
+    const float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 yy = __fmul2_rn(y, y);
+    const float2 h = __fmul2_rn(r2, yy);
+    const float2 y3 = __fmul2_rn(yy, y);
+    const float2 e3 = __ffma2_rn(h, make_float2(-1.5f, -1.5f), make_float2(1.5f, 1.5f));
+    const float2 f = __ffma2_rn(y3, e3, y3);
+    ax = __ffma2_rn(f, dx, ax);
+    ay = __ffma2_rn(f, dy, ay);
+    az = __ffma2_rn(f, dz, az);
 }
 
 // Two sinks against one source with Blackwell's paired FP32 instructions
@@ -158,20 +230,26 @@ __device__ __forceinline__ void pair_force2(const float2 qx, const float2 qy, co
         az = __ffma2_rn(f, dz, az);
         return;
     }
-    const float2 fmin2 = make_float2(FLT_MIN, FLT_MIN);
-    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, fmin2)));
-    float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-    const float2 t = __fmul2_rn(r2, y);
-    const float2 h = __fmul2_rn(t, y);
-    const float2 e = __ffma2_rn(h, mhalf, half);
-    y = __ffma2_rn(y, e, y);
-    const float2 r = __ffma2_rn(t, e, t);
-    const float2 y3 = __fmul2_rn(__fmul2_rn(y, y), y);
-    const float2 g = __ffma2_rn(__ffma2_rn(a2, r, a1), r, a0);
-    const float2 f = make_float2(fminf(y3.x, g.x), fminf(y3.y, g.y));
-    ax = __ffma2_rn(f, dx, ax);
-    ay = __ffma2_rn(f, dy, ay);
-    az = __ffma2_rn(f, dz, az);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(FLT_MIN, FLT_MIN))));
+    tail2_spline(dx, dy, dz, r2, ax, ay, az, a0, a1, a2);
+}
+
+// One pair with a source in a cell at Chebyshev distance 2 from the sink's
+// cell: r >= 1 cell width > eps, so the spline law is Newtonian there and the
+// pair takes tail_newton: 14 FP32-pipe operations + 1 SFU.
+__device__ __forceinline__ void pair_force_far(const float4 q, float xi, float yi, float zi, float &ax, float &ay,
+                                               float &az)
+{
+    const float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
+    tail_newton(dx, dy, dz, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), ax, ay, az);
+}
+
+// pair_force_far for two sinks with paired FP32 instructions (same arithmetic per lane)
+__device__ __forceinline__ void pair_force2_far(const float2 qx, const float2 qy, const float2 qz, const float2 nx,
+                                                const float2 ny, const float2 nz, float2 &ax, float2 &ay, float2 &az)
+{
+    const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
+    tail2_newton(dx, dy, dz, __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx))), ax, ay, az);
 }
 
 // one pair of the adjoint: grad += J(d) (w_j - w_k), J = f I + (f'/r) d d^T
@@ -217,8 +295,30 @@ __device__ __forceinline__ void pair_adjoint(const float4 q, const float4 wj, fl
     gz = fmaf(hd, dz, fmaf(f, uz, gz));
 }
 
-// 125-entry neighbour table of `cell`: tstart[t] = first particle, tpre[t] =
-// exclusive prefix of counts, tpre[125] = total.  t = (dx+2)*25 + (dy+2)*5 + (dz+2).
+// Order of the neighbour table: the 27 cells within one cell of the sink cell
+// (positions 0..26), then the 98 cells at Chebyshev distance 2, each group in
+// (dx, dy, dz) lexicographic order.  code[p] = (dx+2)*25 + (dy+2)*5 + (dz+2).
+constexpr int kNear = 27;
+struct NbrOrder {
+    unsigned char code[kNbr];
+};
+constexpr NbrOrder make_nbr_order()
+{
+    NbrOrder o{};
+    int p = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int t = 0; t < kNbr; ++t) {
+            const int dx = t / 25 - 2, dy = (t / 5) % 5 - 2, dz = t % 5 - 2;
+            const bool near = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
+            if (near == (pass == 0)) o.code[p++] = static_cast<unsigned char>(t);
+        }
+    return o;
+}
+__device__ const NbrOrder kNbrOrder = make_nbr_order();
+
+// 125-entry neighbour table of `cell` in kNbrOrder: tstart[p] = first particle,
+// tpre[p] = exclusive prefix of counts, tpre[125] = total, so sources
+// [tpre[0], tpre[27]) are the near cells' and [tpre[27], total) the far cells'.
 __device__ __forceinline__ int build_table(const BoxDev &bx, int cell, int *tstart, int *tpre, int lane)
 {
     const int C = bx.cpd;
@@ -227,9 +327,10 @@ __device__ __forceinline__ int build_table(const BoxDev &bx, int cell, int *tsta
     int local = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int t = 4 * lane + u;
+        const int p = 4 * lane + u;
         int c = 0;
-        if (t < kNbr) {
+        if (p < kNbr) {
+            const int t = __ldg(&kNbrOrder.code[p]);
             int nx = cx + t / 25 - 2, ny = cy + (t / 5) % 5 - 2, nz = cz + t % 5 - 2;
             nx += nx < 0 ? C : 0; nx -= nx >= C ? C : 0;
             ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
@@ -237,7 +338,7 @@ __device__ __forceinline__ int build_table(const BoxDev &bx, int cell, int *tsta
             const int n = (nx * C + ny) * C + nz;
             const int s0 = __ldg(bx.cell_start + n);
             c = __ldg(bx.cell_start + n + 1) - s0;
-            tstart[t] = s0;
+            tstart[p] = s0;
         }
         cnt[u] = c;
         local += c;
@@ -251,8 +352,8 @@ __device__ __forceinline__ int build_table(const BoxDev &bx, int cell, int *tsta
     int run = incl - local;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int t = 4 * lane + u;
-        if (t <= kNbr) tpre[t] = run;
+        const int p = 4 * lane + u;
+        if (p <= kNbr) tpre[p] = run;
         run += cnt[u];
     }
     const int total = __shfl_sync(kFull, incl, 31);
@@ -260,7 +361,7 @@ __device__ __forceinline__ int build_table(const BoxDev &bx, int cell, int *tsta
     return total;
 }
 
-// neighbour-table slot of flat source index f: tpre[t] <= f < tpre[t+1]
+// neighbour-table position of flat source index f: tpre[p] <= f < tpre[p+1]
 __device__ __forceinline__ int find_cell(const int *tpre, int f)
 {
     int lo = 0, hi = kNbr;
@@ -273,8 +374,8 @@ __device__ __forceinline__ int find_cell(const int *tpre, int f)
 }
 
 // Gather sources [base, base + B) of the flattened neighbourhood into buf
-// (cp.async); entries past `total` become far-away padding.  The table slot
-// of each gathered entry (plus one; 0 = padding) goes to ts[] for the shift pass.
+// (cp.async); entries past `total` become far-away padding.  The offset code
+// of each gathered entry's cell (plus one; 0 = padding) goes to ts[] for the shift pass.
 template <int B, bool ADJ>
 __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float4 *wbuf, const int *tstart,
                                             const int *tpre, int base, int total, int lane, unsigned char *ts)
@@ -284,11 +385,11 @@ __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float
         const int f = base + m * 32 + lane;
         const int slot = m * 32 + lane;
         if (f < total) {
-            const int t = find_cell(tpre, f);
-            const int src = tstart[t] + (f - tpre[t]);
+            const int p = find_cell(tpre, f);
+            const int src = tstart[p] + (f - tpre[p]);
             cp_async16(buf + slot, bx.pos + src);
             if (ADJ) cp_async16(wbuf + slot, bx.cot + src);
-            ts[slot] = static_cast<unsigned char>(t + 1);
+            ts[slot] = static_cast<unsigned char>(__ldg(&kNbrOrder.code[p]) + 1);
         } else {
             buf[slot] = make_float4(kFar, kFar, kFar, 0.f);
             if (ADJ) wbuf[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -382,6 +483,11 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
                  e22 = make_float2(eps2, eps2);
 
     const int total = build_table(bx, item.cell, tstart, tpre, lane);
+    constexpr bool FARSPLIT = NF_FAR_LAW && SOFT == 0;
+    // warp vote in the near cells for lanes holding 2 or 4 sinks (with one sink the
+    // vote costs more issue slots than the spline tail it saves).  eps2 >= 2^-40 by
+    // the softening-length bound, so a self pair's r^2 = FLT_MIN is always below it.
+    constexpr bool VOTE = NF_NEAR_VOTE && FARSPLIT && !ADJ && SS >= 2;
     // the whole flattened neighbourhood, or this item's piece of it
     int src_lo = 0, src_hi = total;
     if (item.piece >= 0) {
@@ -404,22 +510,74 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
         stage_shift<B>(buf, lane, tslot + (r & 1) * B);
         __syncwarp();
         const int nr = min(B, src_hi - src_lo - r * B);
+        // this round's entries [0, nn) come from the 27 near cells and take the
+        // full law; [nn, nr) come from far cells (spline law only: Plummer
+        // softening acts at every distance)
+        const int nn = (FARSPLIT && !ADJ) ? max(0, min(nr, tpre[kNear] - (src_lo + r * B))) : nr;
         if (SPLIT) {
-            for (int j = my_split; j < nr; j += splits) {
+            int j = my_split;
+            for (; j < nn; j += splits) {
                 if (ADJ)
                     pair_adjoint<SOFT>(buf[j], wbuf[j], xi[0], yi[0], zi[0], wx[0], wy[0], wz[0], px[0], py[0], pz[0], a0,
                                  a1, a2, eps2);
                 else
                     pair_force<SOFT>(buf[j], xi[0], yi[0], zi[0], px[0], py[0], pz[0], a0, a1, a2, eps2);
             }
+            if (FARSPLIT && !ADJ)
+                for (; j < nr; j += splits) pair_force_far(buf[j], xi[0], yi[0], zi[0], px[0], py[0], pz[0]);
         } else {
             constexpr int U = NF_SRC_UNROLL;
-            const int nru = (nr + U - 1) / U * U;   // padding entries add exact zeros
-            for (int j = 0; j < nru; j += U) {
+            // padding entries add exact zeros under either law; the near loop's last
+            // step may take up to U - 1 far entries, which the full law treats exactly
+            const int nru = (nr + U - 1) / U * U;
+            const int nnu = (nn + U - 1) / U * U;
+            for (int j = 0; j < nnu; j += U) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const float4 q = buf[j + u];
-                    if (PACK) {
+                    if (VOTE && PACK) {
+                        // a near source takes the spline tail only when some sink of the
+                        // warp lies within eps of it (self pairs included: r^2 = FLT_MIN)
+                        const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
+                                     qz = make_float2(q.z, q.z);
+                        float2 dx[SP], dy[SP], dz[SP], r2[SP];
+                        float m = 0.f;
+#pragma unroll
+                        for (int k = 0; k < SP; ++k) {
+                            dx[k] = __fadd2_rn(qx, nx2[k]);
+                            dy[k] = __fadd2_rn(qy, ny2[k]);
+                            dz[k] = __fadd2_rn(qz, nz2[k]);
+                            r2[k] = __ffma2_rn(dz[k], dz[k], __ffma2_rn(dy[k], dy[k],
+                                               __ffma2_rn(dx[k], dx[k], make_float2(FLT_MIN, FLT_MIN))));
+                            const float mk = fminf(r2[k].x, r2[k].y);
+                            m = k == 0 ? mk : fminf(m, mk);
+                        }
+                        if (__any_sync(kFull, m < eps2)) {
+#pragma unroll
+                            for (int k = 0; k < SP; ++k)
+                                tail2_spline(dx[k], dy[k], dz[k], r2[k], ax2[k], ay2[k], az2[k], a02, a12, a22);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < SP; ++k) tail2_newton(dx[k], dy[k], dz[k], r2[k], ax2[k], ay2[k], az2[k]);
+                        }
+                    } else if (VOTE) {
+                        float dx[SS], dy[SS], dz[SS], r2[SS];
+                        float m = 0.f;
+#pragma unroll
+                        for (int s = 0; s < SS; ++s) {
+                            dx[s] = q.x - xi[s]; dy[s] = q.y - yi[s]; dz[s] = q.z - zi[s];
+                            r2[s] = fmaf(dz[s], dz[s], fmaf(dy[s], dy[s], fmaf(dx[s], dx[s], FLT_MIN)));
+                            m = s == 0 ? r2[s] : fminf(m, r2[s]);
+                        }
+                        if (__any_sync(kFull, m < eps2)) {
+#pragma unroll
+                            for (int s = 0; s < SS; ++s)
+                                tail_spline(dx[s], dy[s], dz[s], r2[s], px[s], py[s], pz[s], a0, a1, a2);
+                        } else {
+#pragma unroll
+                            for (int s = 0; s < SS; ++s) tail_newton(dx[s], dy[s], dz[s], r2[s], px[s], py[s], pz[s]);
+                        }
+                    } else if (PACK) {
                         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
                                      qz = make_float2(q.z, q.z);
 #pragma unroll
@@ -439,6 +597,23 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
                     }
                 }
             }
+            if (FARSPLIT && !ADJ)
+                for (int j = nnu; j < nru; j += U) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const float4 q = buf[j + u];
+                        if (PACK) {
+                            const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
+                                         qz = make_float2(q.z, q.z);
+#pragma unroll
+                            for (int k = 0; k < SP; ++k)
+                                pair_force2_far(qx, qy, qz, nx2[k], ny2[k], nz2[k], ax2[k], ay2[k], az2[k]);
+                        } else {
+#pragma unroll
+                            for (int s = 0; s < SS; ++s) pair_force_far(q, xi[s], yi[s], zi[s], px[s], py[s], pz[s]);
+                        }
+                    }
+                }
         }
         if (COMP) {
             if (PACK) {

@@ -59,6 +59,9 @@ def test_create_rejects_bad_arguments_without_gpu(libnf):
     assert L.nf_create(9, 3, 1e-3, 1.0, ctypes.byref(h)) == nfb.NF_EINVAL       # R != 2
     assert L.nf_create(9, 2, 0.2, 1.0, ctypes.byref(h)) == nfb.NF_EINVAL        # eps >= cell width
     assert L.nf_create(9, 2, 0.0, 1.0, ctypes.byref(h)) == nfb.NF_EINVAL        # eps <= 0
+    w = 1.0 / 9
+    assert L.nf_create(9, 2, w * 2.0**-21, 1.0, ctypes.byref(h)) == nfb.NF_EINVAL   # eps < 2^-20 cell widths
+    assert b"2^-20" in L.nf_last_error(None)
     assert L.nf_create(9, 2, 1e-3, -1.0, ctypes.byref(h)) == nfb.NF_EINVAL      # box <= 0
     assert L.nf_create(2000, 2, 1e-6, 1.0, ctypes.byref(h)) == nfb.NF_EINVAL    # cpd^3 >= 2^31
     assert h.value is None

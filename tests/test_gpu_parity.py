@@ -130,6 +130,27 @@ def test_one_dense_cell_many_tiles():
     _check_forces(acc, ref, sa)
 
 
+def test_softening_close_to_the_cell_width():
+    """eps = 0.95 cell widths: many near-cell pairs fall inside eps (across cell
+    faces, coincident copies included), far-cell pairs start at u = 1.05; dense
+    clumps on cell faces give 1-, 2- and 4-sink tiles."""
+    cpd = 7
+    rng = np.random.default_rng(17)
+    w = 1.0 / cpd
+    centres = (rng.integers(0, cpd, (6, 3)) + np.array([0.0, 0.5, 0.5])) * w   # on x faces
+    clumps = [c + 0.25 * w * rng.standard_normal((600, 3)) for c in centres]
+    X = np.concatenate([rng.random((2000, 3))] + clumps)
+    X = np.concatenate([X, X[rng.choice(len(X), 50, replace=False)]])           # coincident copies
+    X = np.mod(X, 1.0)
+    eps = 0.95 * w
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    assert b.counts.max() > 64
+    acc = nf.forces()
+    ref, sa, _ = oracle.forces(b, eps, with_sumabs=True)
+    _check_forces(acc, ref, sa)
+
+
 def test_cpd5_every_pair_once_against_bruteforce():
     cpd = 5
     X, _ = gen.clustered(3000, np.random.default_rng(5), 3, 0.1, 0.3)
