@@ -64,6 +64,9 @@ namespace {
 #ifndef NF_NEAR_VOTE
 #define NF_NEAR_VOTE 1   // near-cell sources take the Newtonian tail unless a warp lane is within eps
 #endif
+#ifndef NF_PAIR_SOURCES
+#define NF_PAIR_SOURCES 1   // lanes holding one sink evaluate two sources per paired FP32 instruction
+#endif
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
@@ -399,20 +402,46 @@ __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float
     cp_async_commit();
 }
 
-// add the integer cell offset of each of this lane's landed entries
-template <int B>
+// add the integer cell offset of each of this lane's landed entries; with SOA
+// the round is then rewritten in place as three arrays x[B], y[B], z[B] (the
+// layout the source-paired loops read two sources at a time from)
+template <int B, bool SOA>
 __device__ __forceinline__ void stage_shift(float4 *buf, int lane, const unsigned char *ts)
 {
+    if constexpr (SOA) {
+        float4 v[B / 32];
 #pragma unroll
-    for (int m = 0; m < B / 32; ++m) {
-        const int t1 = ts[m * 32 + lane];
-        if (t1) {
-            const int t = t1 - 1;
-            float4 v = buf[m * 32 + lane];
-            v.x += static_cast<float>(t / 25 - 2);
-            v.y += static_cast<float>((t / 5) % 5 - 2);
-            v.z += static_cast<float>(t % 5 - 2);
-            buf[m * 32 + lane] = v;
+        for (int m = 0; m < B / 32; ++m) {
+            const int t1 = ts[m * 32 + lane];
+            v[m] = buf[m * 32 + lane];
+            if (t1) {
+                const int t = t1 - 1;
+                v[m].x += static_cast<float>(t / 25 - 2);
+                v[m].y += static_cast<float>((t / 5) % 5 - 2);
+                v[m].z += static_cast<float>(t % 5 - 2);
+            }
+        }
+        __syncwarp();   // every lane has read its entries before any array entry is written over them
+        float *xs = reinterpret_cast<float *>(buf);
+#pragma unroll
+        for (int m = 0; m < B / 32; ++m) {
+            const int slot = m * 32 + lane;
+            xs[slot] = v[m].x;
+            xs[B + slot] = v[m].y;
+            xs[2 * B + slot] = v[m].z;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < B / 32; ++m) {
+            const int t1 = ts[m * 32 + lane];
+            if (t1) {
+                const int t = t1 - 1;
+                float4 v = buf[m * 32 + lane];
+                v.x += static_cast<float>(t / 25 - 2);
+                v.y += static_cast<float>((t / 5) % 5 - 2);
+                v.z += static_cast<float>(t % 5 - 2);
+                buf[m * 32 + lane] = v;
+            }
         }
     }
 }
@@ -467,7 +496,12 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
         }
     }
     const float a0 = bx.a0, a1 = bx.a1, a2 = bx.a2, eps2 = bx.eps2;
+    // paired FP32 instructions: lanes with 2 or 4 sinks pair two sinks against one
+    // source (PACK); lanes with one sink pair one sink against two sources
+    // (PAIRSRC: even and odd sources of a round go to the two halves of a float2
+    // partial sum, both folded into the sink's sum)
     constexpr bool PACK = NF_PACKED && !ADJ && SS >= 2;
+    constexpr bool PAIRSRC = NF_PAIR_SOURCES && !ADJ && SS == 1;
     constexpr int SP = SS >= 2 ? SS / 2 : 1;
     float2 nx2[SP], ny2[SP], nz2[SP], ax2[SP], ay2[SP], az2[SP];
     if (PACK) {
@@ -479,15 +513,23 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
             ax2[k] = ay2[k] = az2[k] = make_float2(0.f, 0.f);
         }
     }
+    if (PAIRSRC) {
+        nx2[0] = make_float2(-xi[0], -xi[0]);
+        ny2[0] = make_float2(-yi[0], -yi[0]);
+        nz2[0] = make_float2(-zi[0], -zi[0]);
+        ax2[0] = ay2[0] = az2[0] = make_float2(0.f, 0.f);
+    }
     const float2 a02 = make_float2(a0, a0), a12 = make_float2(a1, a1), a22 = make_float2(a2, a2),
                  e22 = make_float2(eps2, eps2);
 
     const int total = build_table(bx, item.cell, tstart, tpre, lane);
     constexpr bool FARSPLIT = NF_FAR_LAW && SOFT == 0;
-    // warp vote in the near cells for lanes holding 2 or 4 sinks (with one sink the
-    // vote costs more issue slots than the spline tail it saves).  eps2 >= 2^-40 by
+    // warp vote in the near cells for lanes holding 2 or 4 sinks, or one sink with
+    // source pairs (for one sink and one source the vote costs more issue slots
+    // than the spline tail it saves).  eps2 >= 2^-40 by
     // the softening-length bound, so a self pair's r^2 = FLT_MIN is always below it.
     constexpr bool VOTE = NF_NEAR_VOTE && FARSPLIT && !ADJ && SS >= 2;
+    constexpr bool VOTE1 = NF_NEAR_VOTE && FARSPLIT && PAIRSRC && !SPLIT;   // one sink, source pairs
     // the whole flattened neighbourhood, or this item's piece of it
     int src_lo = 0, src_hi = total;
     if (item.piece >= 0) {
@@ -507,14 +549,57 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
         } else {
             cp_async_wait_0();
         }
-        stage_shift<B>(buf, lane, tslot + (r & 1) * B);
+        stage_shift<B, PAIRSRC>(buf, lane, tslot + (r & 1) * B);
         __syncwarp();
         const int nr = min(B, src_hi - src_lo - r * B);
         // this round's entries [0, nn) come from the 27 near cells and take the
         // full law; [nn, nr) come from far cells (spline law only: Plummer
         // softening acts at every distance)
         const int nn = (FARSPLIT && !ADJ) ? max(0, min(nr, tpre[kNear] - (src_lo + r * B))) : nr;
-        if (SPLIT) {
+        const float2 *xs2 = reinterpret_cast<const float2 *>(buf);   // PAIRSRC layout: x, y, z arrays
+        const float2 *ys2 = xs2 + B / 2, *zs2 = xs2 + B;
+        if (SPLIT && PAIRSRC) {
+            // source pair m = entries 2m, 2m + 1; the pair holding the last near entry
+            // takes the full law (exact for its far partner); entries >= nr are padding
+            const int nnp = (nn + 1) >> 1, nrp = (nr + 1) >> 1;
+            int m = my_split;
+            for (; m < nnp; m += splits)
+                pair_force2<SOFT>(xs2[m], ys2[m], zs2[m], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0], a02, a12,
+                                  a22, e22);
+            if (FARSPLIT)
+                for (; m < nrp; m += splits)
+                    pair_force2_far(xs2[m], ys2[m], zs2[m], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0]);
+        } else if (PAIRSRC) {
+            constexpr int U2 = NF_SRC_UNROLL / 2;
+            const int nrp = (nr + 2 * U2 - 1) / (2 * U2) * U2;   // padding pairs add exact zeros
+            const int nnp = FARSPLIT ? (nn + 2 * U2 - 1) / (2 * U2) * U2 : nrp;
+            for (int m = 0; m < nnp; m += U2) {
+#pragma unroll
+                for (int u = 0; u < U2; ++u) {
+                    const float2 qx = xs2[m + u], qy = ys2[m + u], qz = zs2[m + u];
+                    if (VOTE1) {
+                        const float2 dx = __fadd2_rn(qx, nx2[0]), dy = __fadd2_rn(qy, ny2[0]),
+                                     dz = __fadd2_rn(qz, nz2[0]);
+                        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy,
+                                                     __ffma2_rn(dx, dx, make_float2(FLT_MIN, FLT_MIN))));
+                        if (__any_sync(kFull, fminf(r2.x, r2.y) < eps2))
+                            tail2_spline(dx, dy, dz, r2, ax2[0], ay2[0], az2[0], a02, a12, a22);
+                        else
+                            tail2_newton(dx, dy, dz, r2, ax2[0], ay2[0], az2[0]);
+                    } else {
+                        pair_force2<SOFT>(qx, qy, qz, nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0], a02, a12,
+                                          a22, e22);
+                    }
+                }
+            }
+            if (FARSPLIT)
+                for (int m = nnp; m < nrp; m += U2) {
+#pragma unroll
+                    for (int u = 0; u < U2; ++u)
+                        pair_force2_far(xs2[m + u], ys2[m + u], zs2[m + u], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0],
+                                        az2[0]);
+                }
+        } else if (SPLIT) {
             int j = my_split;
             for (; j < nn; j += splits) {
                 if (ADJ)
@@ -616,7 +701,10 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
                 }
         }
         if (COMP) {
-            if (PACK) {
+            if (PAIRSRC) {
+                comp_fold_smem(comp + lane, ax2[0].x, ay2[0].x, az2[0].x);
+                comp_fold_smem(comp + lane, ax2[0].y, ay2[0].y, az2[0].y);
+            } else if (PACK) {
 #pragma unroll
                 for (int k = 0; k < SP; ++k) {
                     comp_fold_smem(comp + lane + 32 * (2 * k), ax2[k].x, ay2[k].x, az2[k].x);
@@ -628,6 +716,11 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
             }
         }
         __syncwarp();
+    }
+    if (PAIRSRC && !COMP) {
+        px[0] = ax2[0].x + ax2[0].y;
+        py[0] = ay2[0].x + ay2[0].y;
+        pz[0] = az2[0].x + az2[0].y;
     }
     if (PACK && !COMP) {
 #pragma unroll
