@@ -282,7 +282,7 @@ int nf_tune(nf_t *nf, char *report, int report_len);
  *   stream         cudaStream_t for all work (NULL = legacy default stream)
  *   err, err_len   optional buffer for a one-line message
  * No cudaMalloc, cudaFree or other allocating call is made: the work list
- * and counters live in one fixed device array of 8,390,400 bytes that every GPU
+ * and counters live in one fixed device array of 9,439,488 bytes that every GPU
  * loading the library holds until exit.  Its device address is looked up on
  * the first call on each device, so make that first call before any stream
  * capture.  Calls share that array and it keeps the last call's contents:

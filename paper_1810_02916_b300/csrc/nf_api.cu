@@ -67,8 +67,8 @@ struct nf_box {
     double *partials = nullptr;
     int *split_k = nullptr, *split_p = nullptr, *split_r = nullptr;
     void *split_scan = nullptr;
-    const int **nbr_ptr = nullptr;    // device copy of &offsets' current address (neighbourhood sizes)
-    const int *h_nbr = nullptr;
+    int *nbr = nullptr;               // sources in each cell's neighbourhood
+    const int **nbr_ptr = nullptr;    // device copy of nbr's address (the split planner reads boxes' tables)
     long long wf = 0;                 // resident warps (<= 32 per SM) x balance factor 4
     int reduce_cap = 0;
     void *dt_tmp = nullptr;           // time-step reductions
@@ -297,16 +297,15 @@ int upload_box(nf_t *nf, float4 *acc_out, double *acc64, const float4 *cot)
 // items of this box (all classes, largest first) into nf->items
 int plan(nf_t *nf)
 {
+    // neighbourhood sizes and the pass's pair count, the items (occupancy classes, then
+    // lane items), then the source split
+    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->pairs, nf->counts, nf->nbr, nf->stream));
     NF_CK(nf::zero_device_int(nf->n_raw, nf->stream));
     for (int cls = 0; cls < nf::kClasses; ++cls)
-        NF_CK(nf::plan_items_class(nf->cell_start, nf->ncell, 0, cls, nf->items_raw, nf->n_raw, nf->counts,
+        NF_CK(nf::plan_items_class(nf->cell_start, nf->nbr, nf->ncell, 0, cls, nf->items_raw, nf->n_raw, nf->counts,
                                    nf->offsets, nf->scan_tmp, nf->stream));
-    // neighbourhood sizes (left in offsets) and the pass's pair count, then the source split
-    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->pairs, nf->counts, nf->offsets, nf->stream));
-    if (nf->h_nbr != nf->offsets) {   // offsets and cell_start trade buffers in nf_set_particles
-        nf->h_nbr = nf->offsets;
-        NF_CK(cudaMemcpyAsync(nf->nbr_ptr, &nf->h_nbr, sizeof(int *), cudaMemcpyHostToDevice, nf->stream));
-    }
+    NF_CK(nf::plan_lane_items(nf->cell_start, nf->nbr, nf->cpd, 0, nf->items_raw, nf->n_raw, nf->counts,
+                              nf->offsets, nf->scan_tmp, nf->stream));
     NF_CK(nf::split_items(nf->items_raw, nf->n_raw, static_cast<int>(nf->item_cap), nf->nbr_ptr, nf->pairs, nf->wf,
                           kSplitFloor, nf->split_k, nf->split_p, nf->split_r, nf->split_scan, nf->items,
                           nf->n_items, nf->pieces, nf->reduces, nf->n_reduce, nf->stream));
@@ -486,7 +485,7 @@ int nf_create(int cpd, int R, double eps, double box, nf_t **out)
     }
     const size_t cells = sizeof(int) * (static_cast<size_t>(nf->ncell) + 2);
     if ((rc = dalloc(nf, &nf->cell_start, cells)) || (rc = dalloc(nf, &nf->counts, cells)) ||
-        (rc = dalloc(nf, &nf->offsets, cells)) ||
+        (rc = dalloc(nf, &nf->offsets, cells)) || (rc = dalloc(nf, &nf->nbr, cells)) ||
         (rc = dalloc(nf, &nf->scan_tmp, nf::scan_temp_bytes(static_cast<int64_t>(nf->ncell) + 2))) ||
         (rc = dalloc(nf, &nf->n_items, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->queue, sizeof(int) * 4)) ||
         (rc = dalloc(nf, &nf->n_raw, sizeof(int) * 4)) || (rc = dalloc(nf, &nf->n_reduce, sizeof(int) * 4)) ||
@@ -502,8 +501,12 @@ int nf_create(int cpd, int R, double eps, double box, nf_t **out)
     e = cudaMemset(nf->cell_start, 0, cells);
     if (e == cudaSuccess) e = cudaMemset(nf->n_items, 0, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMemset(nf->n_reduce, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) {
+        const int *table = nf->nbr;
+        e = cudaMemcpy(nf->nbr_ptr, &table, sizeof(table), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
-        g_create_error = std::string("cudaMemset: ") + cudaGetErrorString(e);
+        g_create_error = std::string("device initialisation: ") + cudaGetErrorString(e);
         nf_destroy(nf);
         return NF_ECUDA;
     }
@@ -520,7 +523,7 @@ void nf_destroy(nf_t *nf)
     cudaSetDevice(nf->device);
     cudaStreamSynchronize(nf->stream);
     free_particles(nf);
-    dfree(nf->cell_start); dfree(nf->counts); dfree(nf->offsets);
+    dfree(nf->cell_start); dfree(nf->counts); dfree(nf->offsets); dfree(nf->nbr);
     if (nf->scan_tmp) cudaFree(nf->scan_tmp);
     dfree(nf->n_items); dfree(nf->queue); dfree(nf->err); dfree(nf->pairs); dfree(nf->d_box);
     dfree(nf->n_raw); dfree(nf->n_reduce); dfree(nf->nbr_ptr);
@@ -707,7 +710,7 @@ int nf_pair_count(nf_t *nf, int64_t *pairs)
     if (rc) return rc;
     if (!pairs) return fail(nf, NF_EINVAL, "pairs is NULL");
     if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
-    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->pairs, nf->counts, nf->offsets, nf->stream));
+    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->pairs, nf->counts, nf->nbr, nf->stream));
     unsigned long long h = 0;
     NF_CK(cudaMemcpyAsync(&h, nf->pairs, sizeof(h), cudaMemcpyDeviceToHost, nf->stream));
     NF_CK(cudaStreamSynchronize(nf->stream));
@@ -1074,19 +1077,23 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
         if (B.device != nf->device || raw_cap > B.raw_cap || n_total > B.n_cap || nbox > B.nbox_cap) {
             if ((rc = batch_alloc(nf, B, nbox, raw_cap, n_total))) return rc;
         }
-        NF_CK(nf::zero_device_int(B.n_raw, nf->stream));
-        for (int cls = 0; cls < nf::kClasses; ++cls)
-            for (int b = 0; b < nbox; ++b)
-                NF_CK(nf::plan_items_class(boxes[b]->cell_start, boxes[b]->ncell, b, cls, B.items_raw, B.n_raw,
-                                           boxes[b]->counts, boxes[b]->offsets, boxes[b]->scan_tmp, nf->stream));
         std::vector<const int *> nbr(nbox);
         std::vector<const unsigned long long *> prs(nbox);
         for (int b = 0; b < nbox; ++b) {
             nf_t *x = boxes[b];
-            NF_CK(nf::neighbour_pairs(x->cell_start, x->cpd, x->pairs, x->counts, x->offsets, nf->stream));
-            nbr[b] = x->offsets;
+            NF_CK(nf::neighbour_pairs(x->cell_start, x->cpd, x->pairs, x->counts, x->nbr, nf->stream));
+            nbr[b] = x->nbr;
             prs[b] = x->pairs;
         }
+        NF_CK(nf::zero_device_int(B.n_raw, nf->stream));
+        for (int cls = 0; cls < nf::kClasses; ++cls)
+            for (int b = 0; b < nbox; ++b)
+                NF_CK(nf::plan_items_class(boxes[b]->cell_start, boxes[b]->nbr, boxes[b]->ncell, b, cls, B.items_raw,
+                                           B.n_raw, boxes[b]->counts, boxes[b]->offsets, boxes[b]->scan_tmp,
+                                           nf->stream));
+        for (int b = 0; b < nbox; ++b)
+            NF_CK(nf::plan_lane_items(boxes[b]->cell_start, boxes[b]->nbr, boxes[b]->cpd, b, B.items_raw, B.n_raw,
+                                      boxes[b]->counts, boxes[b]->offsets, boxes[b]->scan_tmp, nf->stream));
         NF_CK(cudaMemcpyAsync(B.nbr_ptrs, nbr.data(), sizeof(int *) * nbox, cudaMemcpyHostToDevice, nf->stream));
         NF_CK(cudaMemcpyAsync(B.pair_ptrs, prs.data(), sizeof(void *) * nbox, cudaMemcpyHostToDevice, nf->stream));
         NF_CK(nf::sum_pair_counts(B.pair_ptrs, nbox, B.total, nf->stream));

@@ -41,14 +41,34 @@ struct BoxDev {
 
 // A work item: up to kTile sinks of one cell against its neighbourhood (or a
 // piece of it).  box and sink count share one word: (box << 16) | count.
+//
+// A lane item instead covers a run of consecutive sparse cells [cell, cell + ng)
+// holding at most 32 sinks in all; each lane takes one sink against that sink's
+// own neighbourhood (piece = -1 - ng, so piece <= -2 marks a lane item).
 struct Item {
     int box_count;
     int cell;
     int sink_begin;
-    int piece;                // -1: the whole neighbourhood, final output; else index into pieces
+    int piece;                // -1: the whole neighbourhood, final output; >= 0: index into pieces; <= -2: lane item
 };
 __host__ __device__ inline int item_box(const Item &it) { return it.box_count >> 16; }
 __host__ __device__ inline int item_count(const Item &it) { return it.box_count & 0xffff; }
+__host__ __device__ inline bool item_is_lanes(const Item &it) { return it.piece <= -2; }
+__host__ __device__ inline int item_lane_cells(const Item &it) { return -1 - it.piece; }
+
+// Cells with at most kLaneMaxN particles and at most kLaneMaxT sources in their
+// neighbourhood are computed through lane items (runs of at most kLaneMaxCells
+// cells and 32 sinks); kLaneMaxN = 0 turns lane items off.
+#ifndef NF_LANE_MAX_N
+#define NF_LANE_MAX_N 8
+#endif
+#ifndef NF_LANE_MAX_T
+#define NF_LANE_MAX_T 512
+#endif
+constexpr int kLaneMaxN = NF_LANE_MAX_N;
+constexpr int kLaneMaxT = NF_LANE_MAX_T;
+constexpr int kLaneMaxCells = 32;
+__host__ __device__ inline bool lane_cell(int n, int nbr) { return n == 0 || (n <= kLaneMaxN && nbr <= kLaneMaxT); }
 
 // Sinks of a split item whose partials are summed (in piece order) by reduce_partials.
 struct Reduce {
@@ -97,8 +117,15 @@ cudaError_t count_keys(const uint32_t *keys, int n, int *counts, cudaStream_t st
 // ---- planner (nf_plan.cu) ----
 // Items of one box and one occupancy class, appended at items[*n_items]
 // (*n_items is a device int and is advanced).
-cudaError_t plan_items_class(const int *cell_start, int ncell, int box_index, int cls, Item *items, int *n_items,
-                             int *scratch_counts, int *scratch_offsets, void *scan_temp, cudaStream_t st);
+// nbr: sources in each cell's neighbourhood (neighbour_pairs), which decides
+// the cells left to lane items.
+cudaError_t plan_items_class(const int *cell_start, const int *nbr, int ncell, int box_index, int cls, Item *items,
+                             int *n_items, int *scratch_counts, int *scratch_offsets, void *scan_temp,
+                             cudaStream_t st);
+// Lane items of one box (see lane_cell), appended at items[*n_items] after
+// every occupancy class.  Scratch: cpd^2 + 1 ints each.
+cudaError_t plan_lane_items(const int *cell_start, const int *nbr, int cpd, int box_index, Item *items, int *n_items,
+                            int *scratch_counts, int *scratch_offsets, void *scan_temp, cudaStream_t st);
 cudaError_t zero_device_int(int *p, cudaStream_t st);
 // Split items whose neighbourhood is long against the whole pass into source
 // pieces (see nf_plan.cu).  items_in/n_in: the class-ordered list; nbr[box]:
@@ -113,7 +140,9 @@ cudaError_t split_items(const Item *items_in, const int *n_in, int item_cap, con
 cudaError_t sum_pair_counts(const unsigned long long *const *ptrs, int n, unsigned long long *out, cudaStream_t st);
 cudaError_t reduce_partials(const BoxDev *boxes, const Reduce *reduces, const int *n_reduce, int max_reduce,
                             int adjoint, cudaStream_t st);
-cudaError_t neighbour_pairs(const int *cell_start, int cpd, unsigned long long *pairs, int *tmp_a, int *tmp_b,
+// sources in each cell's 125-cell neighbourhood into nbr (ncell ints; tmp:
+// ncell ints of scratch) and the pass's pair count sum_c n_c nbr_c into *pairs
+cudaError_t neighbour_pairs(const int *cell_start, int cpd, unsigned long long *pairs, int *tmp, int *nbr,
                             cudaStream_t st);
 
 // ---- kick / drift (nf_step.cu) ----

@@ -7,7 +7,7 @@
 // nf_forces_noalloc: it works on the caller's own device arrays (cell table,
 // positions, output) and keeps its work list and counters in one file-scope
 // device array of fixed size, g_scratch below.  Every GPU that loads the
-// library holds that array (8,390,400 bytes) until the process exits.
+// library holds that array (9,439,488 bytes) until the process exits.
 //
 // The host code reaches the array only through the device address returned
 // by cudaGetSymbolAddress: the symbol's name in host code is a host-side
@@ -38,11 +38,13 @@ constexpr size_t kOffDesc = 0;
 constexpr size_t kOffItems = align256(kOffDesc + sizeof(nf::BoxDev));
 constexpr size_t kOffCounts = align256(kOffItems + sizeof(nf::Item) * static_cast<size_t>(kMaxItems));
 constexpr size_t kOffOffsets = align256(kOffCounts + sizeof(int) * kCellInts);
-constexpr size_t kOffScan = align256(kOffOffsets + sizeof(int) * kCellInts);
+constexpr size_t kOffNbr = align256(kOffOffsets + sizeof(int) * kCellInts);
+constexpr size_t kOffScan = align256(kOffNbr + sizeof(int) * kCellInts);
 constexpr size_t kOffWords = align256(kOffScan + sizeof(int) * kScanInts);   // n_items, queue, error flag
-constexpr size_t kScratchBytes = align256(kOffWords + 4 * sizeof(int));
+constexpr size_t kOffPairs = align256(kOffWords + 4 * sizeof(int));          // the pass's pair count
+constexpr size_t kScratchBytes = align256(kOffPairs + sizeof(unsigned long long));
 
-static_assert(kScratchBytes == 8390400, "the documented scratch size is out of date");
+static_assert(kScratchBytes == 9439488, "the documented scratch size is out of date");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -123,9 +125,11 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     nf::Item *items = reinterpret_cast<nf::Item *>(base + kOffItems);
     int *counts = reinterpret_cast<int *>(base + kOffCounts);
     int *offsets = reinterpret_cast<int *>(base + kOffOffsets);
+    int *nbr = reinterpret_cast<int *>(base + kOffNbr);
     void *scan_tmp = base + kOffScan;
     int *words = reinterpret_cast<int *>(base + kOffWords);
     int *n_items = words, *queue = words + 1, *bad = words + 2;
+    unsigned long long *pairs = reinterpret_cast<unsigned long long *>(base + kOffPairs);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int ncell = cpd * cpd * cpd;
 
@@ -149,9 +153,11 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     if (n == 0) return NF_OK;
 
     // work list (items ordered largest cells first), then the descriptor, then the pair kernel
+    NA_CK(nf::neighbour_pairs(cell_start, cpd, pairs, counts, nbr, st));
     NA_CK(nf::zero_device_int(n_items, st));
     for (int cls = 0; cls < nf::kClasses; ++cls)
-        NA_CK(nf::plan_items_class(cell_start, ncell, 0, cls, items, n_items, counts, offsets, scan_tmp, st));
+        NA_CK(nf::plan_items_class(cell_start, nbr, ncell, 0, cls, items, n_items, counts, offsets, scan_tmp, st));
+    NA_CK(nf::plan_lane_items(cell_start, nbr, cpd, 0, items, n_items, counts, offsets, scan_tmp, st));
     const double inv_w = static_cast<double>(cpd) / box;
     const double ec = eps * inv_w;
     nf::BoxDev d{};

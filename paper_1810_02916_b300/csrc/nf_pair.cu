@@ -43,6 +43,7 @@
 // Every item owns its sinks and sums its sources in a fixed order, so the
 // result does not depend on which warp ran which item (bit-reproducible).
 #include <cfloat>
+#include <climits>
 
 #include "nf_internal.cuh"
 
@@ -787,6 +788,91 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
     }
 }
 
+// A lane item (a run of sparse cells, <= 32 sinks): every lane takes one sink
+// against its own neighbourhood, read straight from global memory (L1) as the
+// 25 (dx, dy) columns of five z-cells.  The five cells of a column are one
+// contiguous particle run (two where the column wraps the box in z), and a
+// source's dz follows from the cell boundaries inside the run.  Separations are
+// exact as on the staged path: (x_j + D) - x_i on the 2^-22 grid.  Lanes work
+// independently (no warp-synchronous step), with the full law for every pair.
+template <bool COMP, bool ADJ, int SOFT>
+__device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
+{
+    const int count = item_count(item);
+    if (lane >= count) return;
+    const int C = bx.cpd;
+    const int *cs = bx.cell_start;
+    const int g0 = item.cell, ng = item_lane_cells(item);
+    const int i = item.sink_begin + lane;
+    int c = g0;   // the sink's cell: the last of the run starting at or before i
+    for (int k = 1; k < ng; ++k) c += __ldg(cs + g0 + k) <= i;
+    const int cz = c % C, cy = (c / C) % C, cx = c / (C * C);
+    const float4 p = __ldg(bx.pos + i);
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ADJ) w = __ldg(bx.cot + i);
+    const float a0 = bx.a0, a1 = bx.a1, a2 = bx.a2, eps2 = bx.eps2;
+    Comp3 acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const bool wrap_lo = cz < 2, wrap_hi = cz + 3 > C;   // never both: C >= 5
+    for (int col = 0; col < 25; ++col) {
+        const int dxi = col / 5 - 2, dyi = col % 5 - 2;
+        int nx = cx + dxi, ny = cy + dyi;
+        nx += nx < 0 ? C : 0; nx -= nx >= C ? C : 0;
+        ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
+        const int *row = cs + (nx * C + ny) * C;
+        const float fx = static_cast<float>(dxi), fy = static_cast<float>(dyi);
+        for (int part = 0; part < 2; ++part) {
+            // cells [z0, z1) of the row; the first has z offset dz0
+            int z0, z1, dz0;
+            if (part == 0) {
+                z0 = wrap_lo ? cz - 2 + C : cz - 2;
+                z1 = wrap_lo ? C : min(cz + 3, C);
+                dz0 = -2;
+            } else {
+                if (!wrap_lo && !wrap_hi) break;
+                z0 = 0;
+                z1 = wrap_lo ? cz + 3 : cz + 3 - C;
+                dz0 = wrap_lo ? -cz : C - cz;
+            }
+            const int m = z1 - z0;
+            const int j0 = __ldg(row + z0), j1 = __ldg(row + z1);
+            if (j0 == j1) continue;
+            const int b1 = m > 1 ? __ldg(row + z0 + 1) : INT_MAX;
+            const int b2 = m > 2 ? __ldg(row + z0 + 2) : INT_MAX;
+            const int b3 = m > 3 ? __ldg(row + z0 + 3) : INT_MAX;
+            const int b4 = m > 4 ? __ldg(row + z0 + 4) : INT_MAX;
+            float px = 0.f, py = 0.f, pz = 0.f;
+            for (int j = j0; j < j1; ++j) {
+                const float4 q0 = __ldg(bx.pos + j);
+                const int dz = dz0 + (j >= b1) + (j >= b2) + (j >= b3) + (j >= b4);
+                const float4 q = make_float4(q0.x + fx, q0.y + fy, q0.z + static_cast<float>(dz), 0.f);
+                if (ADJ)
+                    pair_adjoint<SOFT>(q, __ldg(bx.cot + j), p.x, p.y, p.z, w.x, w.y, w.z, px, py, pz, a0, a1, a2,
+                                       eps2);
+                else
+                    pair_force<SOFT>(q, p.x, p.y, p.z, px, py, pz, a0, a1, a2, eps2);
+            }
+            if (COMP) {
+                float s, e;
+                two_sum(acc.hx, px, s, e); acc.hx = s; acc.lx = __fadd_rn(acc.lx, e);
+                two_sum(acc.hy, py, s, e); acc.hy = s; acc.ly = __fadd_rn(acc.ly, e);
+                two_sum(acc.hz, pz, s, e); acc.hz = s; acc.lz = __fadd_rn(acc.lz, e);
+            } else {
+                acc.hx += px; acc.hy += py; acc.hz += pz;
+            }
+        }
+    }
+    const double scale = ADJ ? bx.grad_scale : bx.acc_scale;
+    const double gx = (static_cast<double>(acc.hx) + static_cast<double>(acc.lx)) * scale;
+    const double gy = (static_cast<double>(acc.hy) + static_cast<double>(acc.ly)) * scale;
+    const double gz = (static_cast<double>(acc.hz) + static_cast<double>(acc.lz)) * scale;
+    if (bx.acc64) {
+        double *o = bx.acc64 + 3 * static_cast<int64_t>(i);
+        o[0] = gx; o[1] = gy; o[2] = gz;
+    }
+    if (bx.acc_out)
+        bx.acc_out[i] = make_float4(static_cast<float>(gx), static_cast<float>(gy), static_cast<float>(gz), 0.f);
+}
+
 // per-warp shared memory, in float4 units: staged sources (and cotangents),
 // compensated sums, neighbour table (256 ints), table slots (2 B bytes)
 template <int B, bool COMP, bool ADJ>
@@ -819,7 +905,9 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
         const Item item = items[it];
         const BoxDev &bx = boxes[item_box(item)];
         const int cnt = item_count(item);
-        if (cnt <= 16)
+        if (item_is_lanes(item))
+            run_lanes<COMP, ADJ, SOFT>(bx, item, lane);
+        else if (cnt <= 16)
             run_item<0, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
         else if (cnt <= 32)
             run_item<1, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);

@@ -11,6 +11,9 @@
 // so the persistent kernel takes the longest items first and the short ones
 // fill the tail (load imbalance across cells of very different density is
 // what the paper names as the cause of its late-time slowdown, Section 2.3).
+// Sparse cells with small neighbourhoods (lane_cell) become lane items instead,
+// appended last: runs of consecutive such cells along z with at most 32 sinks,
+// one sink per lane, which spares the tail one warp-wide setup per cell.
 // Nothing here leaves the device: the item count stays in device memory and
 // is read by the pair kernel, so planning needs no host synchronisation.
 #include "nf_internal.cuh"
@@ -42,7 +45,8 @@ __device__ __forceinline__ int items_of_cell(int n)
     return n / kTile + (r ? remainder_pieces(r, tmp) : 0);
 }
 
-__global__ void class_counts(const int *__restrict__ cell_start, int ncell, int cls, int *__restrict__ counts)
+__global__ void class_counts(const int *__restrict__ cell_start, const int *__restrict__ nbr, int ncell, int cls,
+                             int *__restrict__ counts)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c > ncell) return;
@@ -51,17 +55,18 @@ __global__ void class_counts(const int *__restrict__ cell_start, int ncell, int 
         return;
     }
     const int n = cell_start[c + 1] - cell_start[c];
-    counts[c] = (n > 0 && occupancy_class(n) == cls) ? items_of_cell(n) : 0;
+    counts[c] = (!lane_cell(n, nbr[c]) && occupancy_class(n) == cls) ? items_of_cell(n) : 0;
 }
 
-__global__ void emit_items(const int *__restrict__ cell_start, int ncell, int cls, int box,
-                           const int *__restrict__ offsets, const int *__restrict__ base_p, Item *__restrict__ items)
+__global__ void emit_items(const int *__restrict__ cell_start, const int *__restrict__ nbr, int ncell, int cls,
+                           int box, const int *__restrict__ offsets, const int *__restrict__ base_p,
+                           Item *__restrict__ items)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     const int s0 = cell_start[c];
     const int n = cell_start[c + 1] - s0;
-    if (n <= 0 || occupancy_class(n) != cls) return;
+    if (lane_cell(n, nbr[c]) || occupancy_class(n) != cls) return;
     int out = *base_p + offsets[c];
     Item it;
     it.cell = c;
@@ -83,6 +88,67 @@ __global__ void emit_items(const int *__restrict__ cell_start, int ncell, int cl
             begin += sz[q];
         }
     }
+}
+
+// Lane groups of one z-row of cells (row = x * cpd + y): walking z upwards, a
+// group opens at a non-empty lane cell and takes the following cells while each
+// is a lane cell (empty ones included), the sinks stay <= 32 and the cells
+// <= kLaneMaxCells.  With items == nullptr only counts.
+__device__ int lane_row(const int *__restrict__ cs, const int *__restrict__ nbr, int cpd, int row, int box,
+                        Item *items, int out)
+{
+    const int c0 = row * cpd;
+    int groups = 0, g0 = -1, total = 0;
+    int s = cs[c0];
+    for (int z = 0; z <= cpd; ++z) {
+        const int c = c0 + z;
+        int n = 0;
+        bool is_lane = false;
+        if (z < cpd) {
+            const int s1 = cs[c + 1];
+            n = s1 - s;
+            s = s1;
+            is_lane = lane_cell(n, nbr[c]);
+        }
+        if (g0 >= 0) {
+            if (is_lane && total + n <= 32 && c - g0 < kLaneMaxCells) {
+                total += n;
+                continue;
+            }
+            if (items) {
+                Item it;
+                it.box_count = (box << 16) | total;
+                it.cell = g0;
+                it.sink_begin = cs[g0];
+                it.piece = -1 - (c - g0);
+                items[out + groups] = it;
+            }
+            ++groups;
+            g0 = -1;
+        }
+        if (is_lane && n > 0) {
+            g0 = c;
+            total = n;
+        }
+    }
+    return groups;
+}
+
+__global__ void lane_count(const int *__restrict__ cell_start, const int *__restrict__ nbr, int cpd,
+                           int *__restrict__ counts)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rows = cpd * cpd;
+    if (row > rows) return;
+    counts[row] = row < rows ? lane_row(cell_start, nbr, cpd, row, 0, nullptr, 0) : 0;
+}
+
+__global__ void lane_emit(const int *__restrict__ cell_start, const int *__restrict__ nbr, int cpd, int box,
+                          const int *__restrict__ offsets, const int *__restrict__ base_p, Item *__restrict__ items)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= cpd * cpd) return;
+    lane_row(cell_start, nbr, cpd, row, box, items, *base_p + offsets[row]);
 }
 
 __global__ void advance_base(int *__restrict__ base_p, const int *__restrict__ offsets, int ncell)
@@ -155,7 +221,7 @@ __global__ void split_count(const Item *__restrict__ items, const int *__restric
         long long tmax = target / (s > 0 ? s : 1);
         if (tmax < t_floor) tmax = t_floor;
         kk = 1;
-        if (T > tmax) {
+        if (T > tmax && !item_is_lanes(it)) {
             long long q = (T + tmax - 1) / tmax;
             kk = static_cast<int>(q > 64 ? 64 : q);
             pp = kk * static_cast<int>(s);
@@ -291,30 +357,44 @@ cudaError_t zero_device_int(int *p, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t plan_items_class(const int *cell_start, int ncell, int box_index, int cls, Item *items, int *n_items,
-                             int *scratch_counts, int *scratch_offsets, void *scan_temp, cudaStream_t st)
+cudaError_t plan_items_class(const int *cell_start, const int *nbr, int ncell, int box_index, int cls, Item *items,
+                             int *n_items, int *scratch_counts, int *scratch_offsets, void *scan_temp,
+                             cudaStream_t st)
 {
-    class_counts<<<nblocks(static_cast<int64_t>(ncell) + 1, 256), 256, 0, st>>>(cell_start, ncell, cls,
+    class_counts<<<nblocks(static_cast<int64_t>(ncell) + 1, 256), 256, 0, st>>>(cell_start, nbr, ncell, cls,
                                                                                  scratch_counts);
     cudaError_t e =
         exclusive_scan_i32(scratch_counts, scratch_offsets, static_cast<int64_t>(ncell) + 1, scan_temp, st);
     if (e != cudaSuccess) return e;
-    emit_items<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, cls, box_index, scratch_offsets, n_items,
-                                                    items);
+    emit_items<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, nbr, ncell, cls, box_index, scratch_offsets,
+                                                    n_items, items);
     advance_base<<<1, 1, 0, st>>>(n_items, scratch_offsets, ncell);
     return cudaGetLastError();
 }
 
-cudaError_t neighbour_pairs(const int *cell_start, int cpd, unsigned long long *pairs, int *tmp_a, int *tmp_b,
+cudaError_t plan_lane_items(const int *cell_start, const int *nbr, int cpd, int box_index, Item *items, int *n_items,
+                            int *scratch_counts, int *scratch_offsets, void *scan_temp, cudaStream_t st)
+{
+    if (kLaneMaxN <= 0) return cudaSuccess;
+    const int rows = cpd * cpd;
+    lane_count<<<nblocks(static_cast<int64_t>(rows) + 1, 128), 128, 0, st>>>(cell_start, nbr, cpd, scratch_counts);
+    cudaError_t e = exclusive_scan_i32(scratch_counts, scratch_offsets, static_cast<int64_t>(rows) + 1, scan_temp, st);
+    if (e != cudaSuccess) return e;
+    lane_emit<<<nblocks(rows, 128), 128, 0, st>>>(cell_start, nbr, cpd, box_index, scratch_offsets, n_items, items);
+    advance_base<<<1, 1, 0, st>>>(n_items, scratch_offsets, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t neighbour_pairs(const int *cell_start, int cpd, unsigned long long *pairs, int *tmp, int *nbr,
                             cudaStream_t st)
 {
     const int ncell = cpd * cpd * cpd;
-    occupancy<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, tmp_a);
-    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp_a, tmp_b, cpd, 2);
-    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp_b, tmp_a, cpd, 1);
-    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp_a, tmp_b, cpd, 0);
+    occupancy<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, tmp);
+    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr, cpd, 2);
+    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(nbr, tmp, cpd, 1);
+    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr, cpd, 0);
     cudaMemsetAsync(pairs, 0, sizeof(unsigned long long), st);
-    dot_counts<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, tmp_b, ncell, pairs);
+    dot_counts<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, nbr, ncell, pairs);
     return cudaGetLastError();
 }
 

@@ -318,8 +318,9 @@ def test_plummer_adjoint_matches_oracle():
 
 
 @pytest.mark.parametrize("mode", [0, 1], ids=["compensated", "plain"])
-def test_sparse_cells_direct_staging(mode):
-    """About one particle per cell: neighbourhoods of <= 256 sources staged in one direct copy."""
+def test_sparse_cells_lane_items(mode):
+    """About one particle per cell: nearly every cell is computed through lane items
+    (runs of sparse cells, one sink per lane), columns that wrap the box in z included."""
     rng = np.random.default_rng(32)
     cpd = 25
     X = rng.random((20000, 3))
@@ -337,3 +338,29 @@ def test_sparse_cells_direct_staging(mode):
     gref = oracle.vjp(b, eps, W[:, :3].astype(np.float64))
     s = oracle.error_stats(g[:, :3], gref)
     assert s["rms_rel"] <= 1e-5, s
+
+
+def test_lane_items_mixed_occupancy():
+    """Cells of 0..8 particles: lane runs that end at a tiled cell, at 32 sinks, at 32
+    cells (a long empty stretch) and at the row end, next to tiled cells; spline and
+    Plummer laws."""
+    import paper_1810_02916_b300 as nfb
+    cpd = 11
+    rng = np.random.default_rng(41)
+    counts = rng.choice([0, 0, 1, 1, 2, 3, 4, 4, 5, 8], size=cpd ** 3)
+    counts[3 * cpd * cpd: 3 * cpd * cpd + 40] = 0                  # 40 empty cells in a row
+    counts[5 * cpd * cpd + 2 * cpd: 5 * cpd * cpd + 3 * cpd] = 4     # a row of 44 sinks in lane cells
+    cells = np.repeat(np.arange(cpd ** 3), counts)
+    base = np.stack([cells // (cpd * cpd), (cells // cpd) % cpd, cells % cpd], 1)
+    X = (base + rng.random((len(cells), 3))) / cpd
+    X = X[rng.permutation(len(X))]
+    eps = 0.2 / cpd
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    acc = nf.forces()
+    ref, sa, _ = oracle.forces(b, eps, with_sumabs=True)
+    _check_forces(acc, ref, sa)
+    nf.set_softening(nfb.PLUMMER)
+    acc = nf.forces()
+    ref, sa, _ = oracle.forces(b, eps, soft=oracle.PLUMMER, with_sumabs=True)
+    _check_forces(acc, ref, sa)
