@@ -195,17 +195,18 @@ def _launches_per_step(cpd):
     """Kernels the library launches per step (counted from the code; the ncu launch list agrees).
 
     forces: pair kernel + partial reduction = 2.
-    kick-drift: kick, drift, key count (3); radix sort, per 8-bit pass a histogram, three scan
-    kernels and a scatter (5 x passes); gather (1); cell-start scan (3); plan: counter reset (1),
-    5 occupancy classes x (count, three scan kernels, emit, advance) (30), neighbourhood sizes
-    (occupancy, three window sums, pair total: 5), source split (count, three scans of three
-    kernels, expand: 11).
+    kick-drift: kick-drift, sort keys and cell counts (2); radix sort, per 8-bit pass a histogram,
+    three scan kernels and a scatter (5 x passes); gather (1); cell-start scan (3); plan:
+    neighbourhood sizes (occupancy, three window sums, pair total: 5), counter reset (1),
+    5 occupancy classes x (count, three scan kernels, emit, advance) (30), lane items (count,
+    three scan kernels, emit, advance: 6), source split (count, three scans of three kernels,
+    expand: 11).
     """
     ncell = cpd ** 3
     bits = max(1, (ncell - 1).bit_length())
     passes = (bits + 7) // 8
-    plan = 1 + 5 * 6 + 5 + 11
-    kick_drift = 3 + 5 * passes + 1 + 3 + plan
+    plan = 5 + 1 + 5 * 6 + 6 + 11
+    kick_drift = 2 + 5 * passes + 1 + 3 + plan
     return 2 + kick_drift
 
 

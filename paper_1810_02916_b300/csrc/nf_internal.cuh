@@ -146,11 +146,13 @@ cudaError_t neighbour_pairs(const int *cell_start, int cpd, unsigned long long *
                             cudaStream_t st);
 
 // ---- kick / drift (nf_step.cu) ----
-cudaError_t kick(const float4 *vel, const double *acc64, double dt, double inv_w, int n, float4 *vel_new,
-                 int *cap_violations, cudaStream_t st);
-cudaError_t drift(const float4 *pos, const float4 *vel_new, const uint32_t *cell_of, const uint32_t *perm,
-                  double dt, double inv_w, int cpd, int n, uint32_t *key_by_id, uint32_t *val_by_id,
-                  float4 *xq_by_id, float4 *vel_by_id, cudaStream_t st);
+// kick + drift of every particle into particle-id order (xq_by_id.w holds the
+// new cell id's bits); drift-limit violations counted in *cap_violations
+cudaError_t kick_drift(const float4 *pos, const float4 *vel, const double *acc64, const uint32_t *cell_of,
+                       const uint32_t *perm, double dt, double inv_w, int cpd, int n, float4 *xq_by_id,
+                       float4 *vel_by_id, int *cap_violations, cudaStream_t st);
+// sort keys (new cell ids) and values (ids) from kick_drift's output; counts += cell occupancies
+cudaError_t drift_keys(const float4 *xq_by_id, int n, uint32_t *keys, uint32_t *vals, int *counts, cudaStream_t st);
 
 // cell multipoles (nf_multipole.cu)
 int multipole_terms(int order);

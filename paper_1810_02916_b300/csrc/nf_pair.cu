@@ -68,6 +68,9 @@ namespace {
 #ifndef NF_PAIR_SOURCES
 #define NF_PAIR_SOURCES 1   // lanes holding one sink evaluate two sources per paired FP32 instruction
 #endif
+#ifndef NF_LANE_FAR_LAW
+#define NF_LANE_FAR_LAW 1   // lane items: columns at |dx| = 2 or |dy| = 2 take the Newtonian law
+#endif
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
@@ -794,7 +797,8 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
 // contiguous particle run (two where the column wraps the box in z), and a
 // source's dz follows from the cell boundaries inside the run.  Separations are
 // exact as on the staged path: (x_j + D) - x_i on the 2^-22 grid.  Lanes work
-// independently (no warp-synchronous step), with the full law for every pair.
+// independently (no warp-synchronous step); columns at |dx| = 2 or |dy| = 2
+// take the Newtonian law, the others the branch-free law.
 template <bool COMP, bool ADJ, int SOFT>
 __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
 {
@@ -820,6 +824,10 @@ __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
         ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
         const int *row = cs + (nx * C + ny) * C;
         const float fx = static_cast<float>(dxi), fy = static_cast<float>(dyi);
+        const float ox = fx - p.x, oy = fy - p.y;   // exact: the 2^-22 grid, |.| < 3
+        // every lane walks the columns in the same order, so this is warp-uniform: a
+        // column with |dx| = 2 or |dy| = 2 lies beyond eps and takes the Newtonian law
+        const bool far_col = SOFT == 0 && !ADJ && (dxi == -2 || dxi == 2 || dyi == -2 || dyi == 2);
         for (int part = 0; part < 2; ++part) {
             // cells [z0, z1) of the row; the first has z offset dz0
             int z0, z1, dz0;
@@ -841,15 +849,29 @@ __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
             const int b3 = m > 3 ? __ldg(row + z0 + 3) : INT_MAX;
             const int b4 = m > 4 ? __ldg(row + z0 + 4) : INT_MAX;
             float px = 0.f, py = 0.f, pz = 0.f;
-            for (int j = j0; j < j1; ++j) {
-                const float4 q0 = __ldg(bx.pos + j);
-                const int dz = dz0 + (j >= b1) + (j >= b2) + (j >= b3) + (j >= b4);
-                const float4 q = make_float4(q0.x + fx, q0.y + fy, q0.z + static_cast<float>(dz), 0.f);
-                if (ADJ)
+            if (ADJ) {
+                for (int j = j0; j < j1; ++j) {
+                    const float4 q0 = __ldg(bx.pos + j);
+                    const int dz = dz0 + (j >= b1) + (j >= b2) + (j >= b3) + (j >= b4);
+                    const float4 q = make_float4(q0.x + fx, q0.y + fy, q0.z + static_cast<float>(dz), 0.f);
                     pair_adjoint<SOFT>(q, __ldg(bx.cot + j), p.x, p.y, p.z, w.x, w.y, w.z, px, py, pz, a0, a1, a2,
                                        eps2);
-                else
+                }
+            } else if (NF_LANE_FAR_LAW && far_col) {
+                for (int j = j0; j < j1; ++j) {
+                    const float4 q0 = __ldg(bx.pos + j);
+                    const int dz = dz0 + (j >= b1) + (j >= b2) + (j >= b3) + (j >= b4);
+                    // d = x_j + D - x_i, exact (each sum lies on the 2^-22 grid)
+                    const float ddx = q0.x + ox, ddy = q0.y + oy, ddz = q0.z + (static_cast<float>(dz) - p.z);
+                    tail_newton(ddx, ddy, ddz, fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx)), px, py, pz);
+                }
+            } else {
+                for (int j = j0; j < j1; ++j) {
+                    const float4 q0 = __ldg(bx.pos + j);
+                    const int dz = dz0 + (j >= b1) + (j >= b2) + (j >= b3) + (j >= b4);
+                    const float4 q = make_float4(q0.x + fx, q0.y + fy, q0.z + static_cast<float>(dz), 0.f);
                     pair_force<SOFT>(q, p.x, p.y, p.z, px, py, pz, a0, a1, a2, eps2);
+                }
             }
             if (COMP) {
                 float s, e;

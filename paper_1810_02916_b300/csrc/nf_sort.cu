@@ -206,7 +206,8 @@ __global__ void gather_kernel(const uint32_t *__restrict__ perm, const float4 *_
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const uint32_t i = perm[k];
-    pos[k] = xq_by_id[i];
+    const float4 q = xq_by_id[i];
+    pos[k] = make_float4(q.x, q.y, q.z, 0.f);   // w: scratch (the drift's cell id) before the sort
     if (vel) vel[k] = vel_by_id ? vel_by_id[i] : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
