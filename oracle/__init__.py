@@ -56,6 +56,7 @@ def lib():
         _lib.nf_oracle_forces.argtypes = [i64, cint, dbl, dbl, cint, p, p, i64, p, p, p, p, p]
         _lib.nf_oracle_bruteforce.argtypes = [i64, cint, dbl, dbl, cint, i64, p, p, p]
         _lib.nf_oracle_vjp.argtypes = [i64, cint, dbl, dbl, cint, p, p, p, i64, p, p, p]
+        _lib.nf_oracle_cutoff.argtypes = [i64, dbl, dbl, i64, p, p, i64, p, p, p]
         _lib.nf_oracle_law.argtypes = [dbl, dbl, cint]
         _lib.nf_oracle_law.restype = dbl
     return _lib
@@ -166,6 +167,21 @@ def forces(b: Binned, eps: float, sinks=None, R: int = 2, soft: int = SPLINE,
                            _ptr(sinks), _ptr(scell), _ptr(acc), _ptr(sa), ctypes.byref(pairs))
     if with_sumabs:
         return acc, sa, int(pairs.value)
+    return acc
+
+
+def cutoff(b: Binned, eps: float, n_min: int, sinks=None) -> np.ndarray:
+    """FP64 accelerations (box units) with dense far cells (>= n_min particles, Chebyshev
+    distance 2) replaced by the quadrupoles of their 4^3 sub-cells (see nf_oracle_cutoff)."""
+    if sinks is None:
+        sinks = np.arange(b.n, dtype=np.int64)
+    sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+    scell = np.ascontiguousarray(b.cell[sinks], dtype=np.int64)
+    x = np.ascontiguousarray(b.xq, dtype=np.float64)
+    off = np.ascontiguousarray(b.offsets, dtype=np.int64)
+    acc = np.zeros((sinks.size, 3))
+    lib().nf_oracle_cutoff(b.cpd, b.w, float(eps), int(n_min), _ptr(off), _ptr(x), sinks.size, _ptr(sinks),
+                           _ptr(scell), _ptr(acc))
     return acc
 
 

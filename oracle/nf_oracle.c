@@ -129,6 +129,110 @@ void nf_oracle_forces(int64_t cpd, int R, double w, double eps, int soft,
 }
 
 /*
+ * Cut-off acceleration of dense cells (the paper leaves trees for dense
+ * clusters to future versions, Section 2.1, with the opening rule set by the
+ * efficiency-accuracy trade-off; this restates the approximation the library
+ * implements, in plain FP64 loops).  For a sink in cell c:
+ *   - the 27 cells within one cell of c, and every cell at Chebyshev distance
+ *     2 holding fewer than n_min particles, are summed directly with the
+ *     spline law, exactly as nf_oracle_forces does;
+ *   - a cell at distance 2 holding at least n_min particles is replaced by the
+ *     quadrupole expansions of its K^3 sub-cells (K = 4; a particle's sub-cell
+ *     along each axis is floor((x_rel + 1/2) K), kept in 0..K-1).  For a
+ *     sub-cell with M particles, centre of mass X and traceless quadrupole
+ *     Q_ab = sum_j (3 s_a s_b - |s|^2 delta_ab), s = x_j - X, the potential
+ *     sum_j 1/|R + s_j| = M/r + (R.Q.R) / (2 r^5) + O(s^3) (R = X - x_i, the
+ *     dipole term vanishes about X) gives the acceleration
+ *         M R / r^3 - Q R / r^5 + (5/2) (R.Q.R) R / r^7.
+ *     Every particle of such a cell is at least one cell width from the sink,
+ *     beyond any softening length, so the Newtonian law applies.
+ * Arguments as nf_oracle_forces, plus n_min; acc in box units.
+ */
+#define CUT_K 4
+void nf_oracle_cutoff(int64_t cpd, double w, double eps, int64_t n_min,
+                      const int64_t *cell_start, const double *xrel,
+                      int64_t nsink, const int64_t *sink, const int64_t *sink_cell, double *acc)
+{
+    const int R = 2;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t s = 0; s < nsink; s++) {
+        int64_t i = sink[s];
+        int64_t c = sink_cell[s];
+        int64_t cz = c % cpd, cy = (c / cpd) % cpd, cx = c / (cpd * cpd);
+        double xi = xrel[3 * i], yi = xrel[3 * i + 1], zi = xrel[3 * i + 2];
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int dx = -R; dx <= R; dx++)
+            for (int dy = -R; dy <= R; dy++)
+                for (int dz = -R; dz <= R; dz++) {
+                    int64_t n = (wrap(cx + dx, cpd) * cpd + wrap(cy + dy, cpd)) * cpd + wrap(cz + dz, cpd);
+                    int64_t j0 = cell_start[n], j1 = cell_start[n + 1];
+                    int far = abs(dx) == 2 || abs(dy) == 2 || abs(dz) == 2;
+                    if (!far || j1 - j0 < n_min) {
+                        for (int64_t j = j0; j < j1; j++) {
+                            double ddx = ((xrel[3 * j] + dx) - xi) * w;
+                            double ddy = ((xrel[3 * j + 1] + dy) - yi) * w;
+                            double ddz = ((xrel[3 * j + 2] + dz) - zi) * w;
+                            double r = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+                            double f = law_f(r, eps, SOFT_SPLINE);
+                            ax += f * ddx;
+                            ay += f * ddy;
+                            az += f * ddz;
+                        }
+                        continue;
+                    }
+                    for (int sub = 0; sub < CUT_K * CUT_K * CUT_K; sub++) {
+                        int qx = sub / (CUT_K * CUT_K), qy = (sub / CUT_K) % CUT_K, qz = sub % CUT_K;
+                        /* members of the sub-cell: count and centre of mass (cell units, source frame) */
+                        double m = 0.0, X[3] = {0.0, 0.0, 0.0};
+                        for (int64_t j = j0; j < j1; j++) {
+                            int b[3];
+                            for (int a = 0; a < 3; a++) {
+                                int q = (int)floor((xrel[3 * j + a] + 0.5) * CUT_K);
+                                b[a] = q < 0 ? 0 : (q > CUT_K - 1 ? CUT_K - 1 : q);
+                            }
+                            if (b[0] != qx || b[1] != qy || b[2] != qz) continue;
+                            m += 1.0;
+                            for (int a = 0; a < 3; a++) X[a] += xrel[3 * j + a];
+                        }
+                        if (m == 0.0) continue;
+                        for (int a = 0; a < 3; a++) X[a] /= m;
+                        double Q[3][3] = {{0.0}};
+                        for (int64_t j = j0; j < j1; j++) {
+                            int b[3];
+                            for (int a = 0; a < 3; a++) {
+                                int q = (int)floor((xrel[3 * j + a] + 0.5) * CUT_K);
+                                b[a] = q < 0 ? 0 : (q > CUT_K - 1 ? CUT_K - 1 : q);
+                            }
+                            if (b[0] != qx || b[1] != qy || b[2] != qz) continue;
+                            double sv[3], s2 = 0.0;
+                            for (int a = 0; a < 3; a++) {
+                                sv[a] = (xrel[3 * j + a] - X[a]) * w;
+                                s2 += sv[a] * sv[a];
+                            }
+                            for (int a = 0; a < 3; a++)
+                                for (int bb = 0; bb < 3; bb++) Q[a][bb] += 3.0 * sv[a] * sv[bb] - (a == bb ? s2 : 0.0);
+                        }
+                        double Rv[3] = {((X[0] + dx) - xi) * w, ((X[1] + dy) - yi) * w, ((X[2] + dz) - zi) * w};
+                        double r2 = Rv[0] * Rv[0] + Rv[1] * Rv[1] + Rv[2] * Rv[2];
+                        double r = sqrt(r2);
+                        double QR[3], RQR = 0.0;
+                        for (int a = 0; a < 3; a++) {
+                            QR[a] = Q[a][0] * Rv[0] + Q[a][1] * Rv[1] + Q[a][2] * Rv[2];
+                            RQR += Rv[a] * QR[a];
+                        }
+                        double r3 = r2 * r, r5 = r3 * r2, r7 = r5 * r2;
+                        ax += m * Rv[0] / r3 - QR[0] / r5 + 2.5 * RQR * Rv[0] / r7;
+                        ay += m * Rv[1] / r3 - QR[1] / r5 + 2.5 * RQR * Rv[1] / r7;
+                        az += m * Rv[2] / r3 - QR[2] / r5 + 2.5 * RQR * Rv[2] / r7;
+                    }
+                }
+        acc[3 * s] = ax;
+        acc[3 * s + 1] = ay;
+        acc[3 * s + 2] = az;
+    }
+}
+
+/*
  * Brute force over all ordered pairs, written without cell lists: particle j
  * acts on particle i through the one periodic image (shift n L, n in
  * {-1,0,1}^3) whose cell lies at most R cells from i's cell along every axis,

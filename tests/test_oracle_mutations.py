@@ -27,6 +27,11 @@ FORCE_PINS = [
 ]
 VJP_PINS = [lambda: pins.test_vjp_matches_central_differences(0.01),
             lambda: pins.test_vjp_matches_central_differences(0.08)]
+CUT_PINS = [pins.test_cutoff_without_dense_cells_is_the_direct_sum,
+            pins.test_cutoff_with_one_particle_per_subcell_is_exact,
+            pins.test_cutoff_error_of_a_generic_cluster_falls_as_its_size_cubed,
+            pins.test_cutoff_error_of_a_symmetric_cluster_falls_as_its_size_to_the_fourth,
+            pins.test_cutoff_keeps_the_27_near_cells_direct]
 
 MUTANTS = [
     ("spline coefficient", "(10.0 - 15.0 * u + 6.0 * u * u)", "(10.0 - 15.0 * u + 5.0 * u * u)", FORCE_PINS),
@@ -46,6 +51,14 @@ MUTANTS = [
     ("adjoint Jacobian term", "return -3.0 / (r2 * r2 * r);", "return 3.0 / (r2 * r2 * r);", VJP_PINS),
     ("adjoint spline derivative", "(-15.0 / (eps * r) + 12.0 / (eps * eps))", "(-15.0 / (eps * r) + 6.0 / (eps * eps))",
      VJP_PINS),
+    ("cutoff quadrupole sign", "ax += m * Rv[0] / r3 - QR[0] / r5", "ax += m * Rv[0] / r3 + QR[0] / r5", CUT_PINS),
+    ("cutoff radial quadrupole factor", "2.5 * RQR * Rv[1] / r7", "1.5 * RQR * Rv[1] / r7", CUT_PINS),
+    ("cutoff quadrupole trace", "3.0 * sv[a] * sv[bb] - (a == bb ? s2 : 0.0)", "3.0 * sv[a] * sv[bb]", CUT_PINS),
+    ("cutoff centre of mass", "X[a] /= m;", "X[a] /= m + 1.0;", CUT_PINS),
+    ("cutoff sub-cell binning", "floor((xrel[3 * j + a] + 0.5) * CUT_K)", "floor((xrel[3 * j + a] + 0.5) * (CUT_K - 1))",
+     CUT_PINS),
+    ("cutoff near layer", "int far = abs(dx) == 2 || abs(dy) == 2 || abs(dz) == 2;",
+     "int far = abs(dx) >= 1 || abs(dy) >= 1 || abs(dz) >= 1;", CUT_PINS),
 ]
 
 
@@ -56,7 +69,7 @@ def _load_mutant(src_text, tmpdir):
     subprocess.check_call(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, path, "-lm"])
     lib = ctypes.CDLL(so)
     ref = oracle.lib()
-    for name in ("nf_oracle_forces", "nf_oracle_bruteforce", "nf_oracle_vjp", "nf_oracle_law"):
+    for name in ("nf_oracle_forces", "nf_oracle_bruteforce", "nf_oracle_vjp", "nf_oracle_law", "nf_oracle_cutoff"):
         getattr(lib, name).argtypes = getattr(ref, name).argtypes
         getattr(lib, name).restype = getattr(ref, name).restype
     return lib

@@ -411,3 +411,82 @@ def test_multipoles_of_a_symmetric_cell_have_no_odd_terms():
         if (a + bb + k) % 2:
             assert abs(M[c, t]) < 1e-15
     assert M[c, 0] == 100.0
+
+
+# ------------------------------------------------------------------ cut-off acceleration of dense cells
+
+def _far_cell_setup(cluster_cell_rel, sink_rel=(0.0, 0.0, 0.0), cpd=5):
+    """One sink in cell (0,0,0) and a cluster (cell-relative offsets) in cell (2,0,0), Chebyshev distance 2."""
+    w = 1.0 / cpd
+    sink = (np.array([0.5, 0.5, 0.5]) + np.asarray(sink_rel)) * w
+    cl = (np.array([2.5, 0.5, 0.5]) + np.asarray(cluster_cell_rel)) * w
+    X = np.vstack([sink[None, :], cl])
+    b = oracle.bin_positions(X, cpd, 1.0)
+    k = int(np.flatnonzero(b.cell == 0)[0])
+    return b, np.array([k], dtype=np.int64)
+
+
+def test_cutoff_without_dense_cells_is_the_direct_sum():
+    """n_min above every occupancy: the cut-off sum is the direct sum, term for term."""
+    rng = np.random.default_rng(71)
+    X, _ = gen.clustered(4000, rng, 4, 0.05, 0.2)
+    b = oracle.bin_positions(X, 6, 1.0)
+    eps = 0.01 / 6
+    ref = oracle.forces(b, eps)
+    cut = oracle.cutoff(b, eps, n_min=int(b.counts.max()) + 1)
+    assert np.array_equal(ref, cut)
+
+
+def test_cutoff_with_one_particle_per_subcell_is_exact():
+    """A sub-cell holding a single particle has its centre of mass on it and Q = 0."""
+    rng = np.random.default_rng(72)
+    q = np.array([(a, bb, c) for a in range(4) for bb in range(4) for c in range(4)], dtype=np.float64)
+    rel = (q + 0.5) / 4 - 0.5 + (rng.random(q.shape) - 0.5) * 0.2   # one particle inside each sub-cell
+    b, sink = _far_cell_setup(rel, sink_rel=(0.21, -0.13, 0.37))
+    eps = 0.01 / 5
+    ref = oracle.forces(b, eps, sinks=sink)
+    cut = oracle.cutoff(b, eps, n_min=1, sinks=sink)
+    assert np.allclose(cut, ref, rtol=1e-12, atol=0)
+
+
+def _cluster_error(offsets, sigma, sink_rel):
+    centre = np.array([-0.125, 0.125, 0.125])   # centre of sub-cell (1, 2, 2)
+    b, sink = _far_cell_setup(centre + sigma * offsets, sink_rel=sink_rel)
+    eps = 0.01 / 5
+    ref = oracle.forces(b, eps, sinks=sink)
+    cut = oracle.cutoff(b, eps, n_min=1, sinks=sink)
+    return float(np.linalg.norm(cut - ref) / np.linalg.norm(ref))
+
+
+def test_cutoff_error_of_a_generic_cluster_falls_as_its_size_cubed():
+    """The first term the quadrupole expansion drops is the octupole: error ~ sigma^3.
+    (A missing or mis-signed quadrupole would leave an error ~ sigma^2.)"""
+    rng = np.random.default_rng(73)
+    off = rng.standard_normal((40, 3))
+    for sink_rel in [(0.3, -0.2, 0.1), (-0.4, 0.45, -0.3)]:
+        e1 = _cluster_error(off, 0.02, sink_rel)
+        e2 = _cluster_error(off, 0.01, sink_rel)
+        assert 1e-9 < e1 < 1e-3
+        assert 0.09 < e2 / e1 < 0.16, (e1, e2)
+
+
+def test_cutoff_error_of_a_symmetric_cluster_falls_as_its_size_to_the_fourth():
+    """Points at +-s along each axis (and the centre) have no octupole: error ~ sigma^4."""
+    off = np.vstack([np.zeros(3), np.eye(3), -np.eye(3), 0.7 * np.eye(3)[[1, 2, 0]], -0.7 * np.eye(3)[[1, 2, 0]]])
+    e1 = _cluster_error(off, 0.04, (0.3, -0.2, 0.1))
+    e2 = _cluster_error(off, 0.02, (0.3, -0.2, 0.1))
+    assert 1e-10 < e1 < 1e-3
+    assert 0.045 < e2 / e1 < 0.085, (e1, e2)
+
+
+def test_cutoff_keeps_the_27_near_cells_direct():
+    """A dense cell adjacent to the sink's is summed pair by pair even with n_min = 1."""
+    rng = np.random.default_rng(74)
+    cpd, w = 5, 0.2
+    sink = np.array([[0.5, 0.5, 0.5]]) * w
+    near = (np.array([1.5, 1.5, 0.5]) + (rng.random((300, 3)) - 0.5)) * w
+    X = np.vstack([sink, near])
+    b = oracle.bin_positions(X, cpd, 1.0)
+    k = np.flatnonzero(b.cell == 0)
+    eps = 0.01 / cpd
+    assert np.array_equal(oracle.cutoff(b, eps, n_min=1, sinks=k), oracle.forces(b, eps, sinks=k))
