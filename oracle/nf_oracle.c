@@ -149,11 +149,64 @@ void nf_oracle_forces(int64_t cpd, int R, double w, double eps, int soft,
  * Arguments as nf_oracle_forces, plus n_min; acc in box units.
  */
 #define CUT_K 4
+#define CUT_SUB (CUT_K * CUT_K * CUT_K)
+
+static int cut_sub_index(const double *x)
+{
+    int b[3];
+    for (int a = 0; a < 3; a++) {
+        int q = (int)floor((x[a] + 0.5) * CUT_K);
+        b[a] = q < 0 ? 0 : (q > CUT_K - 1 ? CUT_K - 1 : q);
+    }
+    return (b[0] * CUT_K + b[1]) * CUT_K + b[2];
+}
+
+/* count, centre of mass (cell units) and Q (box units^2) of every sub-cell of cell n; 13 doubles per sub-cell */
+static void cut_moments(const int64_t *cell_start, const double *xrel, int64_t n, double w, double *mom)
+{
+    int64_t j0 = cell_start[n], j1 = cell_start[n + 1];
+    for (int sub = 0; sub < CUT_SUB; sub++) {
+        double *o = mom + 13 * sub;
+        double m = 0.0, X[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = j0; j < j1; j++) {
+            if (cut_sub_index(xrel + 3 * j) != sub) continue;
+            m += 1.0;
+            for (int a = 0; a < 3; a++) X[a] += xrel[3 * j + a];
+        }
+        o[0] = m;
+        if (m == 0.0) continue;
+        for (int a = 0; a < 3; a++) X[a] /= m;
+        double Q[3][3] = {{0.0}};
+        for (int64_t j = j0; j < j1; j++) {
+            if (cut_sub_index(xrel + 3 * j) != sub) continue;
+            double sv[3], s2 = 0.0;
+            for (int a = 0; a < 3; a++) {
+                sv[a] = (xrel[3 * j + a] - X[a]) * w;
+                s2 += sv[a] * sv[a];
+            }
+            for (int a = 0; a < 3; a++)
+                for (int bb = 0; bb < 3; bb++) Q[a][bb] += 3.0 * sv[a] * sv[bb] - (a == bb ? s2 : 0.0);
+        }
+        for (int a = 0; a < 3; a++) o[1 + a] = X[a];
+        for (int a = 0; a < 3; a++)
+            for (int bb = 0; bb < 3; bb++) o[4 + 3 * a + bb] = Q[a][bb];
+    }
+}
+
 void nf_oracle_cutoff(int64_t cpd, double w, double eps, int64_t n_min,
                       const int64_t *cell_start, const double *xrel,
                       int64_t nsink, const int64_t *sink, const int64_t *sink_cell, double *acc)
 {
     const int R = 2;
+    const int64_t ncell = cpd * cpd * cpd;
+    /* the moments of every cell at or above n_min, computed once */
+    int64_t *slot = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncell);
+    int64_t ndense = 0;
+    for (int64_t c = 0; c < ncell; c++) slot[c] = cell_start[c + 1] - cell_start[c] >= n_min ? ndense++ : -1;
+    double *mom = (double *)malloc(sizeof(double) * 13 * CUT_SUB * (size_t)(ndense > 0 ? ndense : 1));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < ncell; c++)
+        if (slot[c] >= 0) cut_moments(cell_start, xrel, c, w, mom + 13 * CUT_SUB * slot[c]);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t s = 0; s < nsink; s++) {
         int64_t i = sink[s];
@@ -165,10 +218,9 @@ void nf_oracle_cutoff(int64_t cpd, double w, double eps, int64_t n_min,
             for (int dy = -R; dy <= R; dy++)
                 for (int dz = -R; dz <= R; dz++) {
                     int64_t n = (wrap(cx + dx, cpd) * cpd + wrap(cy + dy, cpd)) * cpd + wrap(cz + dz, cpd);
-                    int64_t j0 = cell_start[n], j1 = cell_start[n + 1];
                     int far = abs(dx) == 2 || abs(dy) == 2 || abs(dz) == 2;
-                    if (!far || j1 - j0 < n_min) {
-                        for (int64_t j = j0; j < j1; j++) {
+                    if (!far || slot[n] < 0) {
+                        for (int64_t j = cell_start[n]; j < cell_start[n + 1]; j++) {
                             double ddx = ((xrel[3 * j] + dx) - xi) * w;
                             double ddy = ((xrel[3 * j + 1] + dy) - yi) * w;
                             double ddz = ((xrel[3 * j + 2] + dz) - zi) * w;
@@ -180,44 +232,17 @@ void nf_oracle_cutoff(int64_t cpd, double w, double eps, int64_t n_min,
                         }
                         continue;
                     }
-                    for (int sub = 0; sub < CUT_K * CUT_K * CUT_K; sub++) {
-                        int qx = sub / (CUT_K * CUT_K), qy = (sub / CUT_K) % CUT_K, qz = sub % CUT_K;
-                        /* members of the sub-cell: count and centre of mass (cell units, source frame) */
-                        double m = 0.0, X[3] = {0.0, 0.0, 0.0};
-                        for (int64_t j = j0; j < j1; j++) {
-                            int b[3];
-                            for (int a = 0; a < 3; a++) {
-                                int q = (int)floor((xrel[3 * j + a] + 0.5) * CUT_K);
-                                b[a] = q < 0 ? 0 : (q > CUT_K - 1 ? CUT_K - 1 : q);
-                            }
-                            if (b[0] != qx || b[1] != qy || b[2] != qz) continue;
-                            m += 1.0;
-                            for (int a = 0; a < 3; a++) X[a] += xrel[3 * j + a];
-                        }
+                    const double *mc = mom + 13 * CUT_SUB * slot[n];
+                    for (int sub = 0; sub < CUT_SUB; sub++) {
+                        const double *o = mc + 13 * sub;
+                        double m = o[0];
                         if (m == 0.0) continue;
-                        for (int a = 0; a < 3; a++) X[a] /= m;
-                        double Q[3][3] = {{0.0}};
-                        for (int64_t j = j0; j < j1; j++) {
-                            int b[3];
-                            for (int a = 0; a < 3; a++) {
-                                int q = (int)floor((xrel[3 * j + a] + 0.5) * CUT_K);
-                                b[a] = q < 0 ? 0 : (q > CUT_K - 1 ? CUT_K - 1 : q);
-                            }
-                            if (b[0] != qx || b[1] != qy || b[2] != qz) continue;
-                            double sv[3], s2 = 0.0;
-                            for (int a = 0; a < 3; a++) {
-                                sv[a] = (xrel[3 * j + a] - X[a]) * w;
-                                s2 += sv[a] * sv[a];
-                            }
-                            for (int a = 0; a < 3; a++)
-                                for (int bb = 0; bb < 3; bb++) Q[a][bb] += 3.0 * sv[a] * sv[bb] - (a == bb ? s2 : 0.0);
-                        }
-                        double Rv[3] = {((X[0] + dx) - xi) * w, ((X[1] + dy) - yi) * w, ((X[2] + dz) - zi) * w};
+                        double Rv[3] = {((o[1] + dx) - xi) * w, ((o[2] + dy) - yi) * w, ((o[3] + dz) - zi) * w};
                         double r2 = Rv[0] * Rv[0] + Rv[1] * Rv[1] + Rv[2] * Rv[2];
                         double r = sqrt(r2);
                         double QR[3], RQR = 0.0;
                         for (int a = 0; a < 3; a++) {
-                            QR[a] = Q[a][0] * Rv[0] + Q[a][1] * Rv[1] + Q[a][2] * Rv[2];
+                            QR[a] = o[4 + 3 * a] * Rv[0] + o[5 + 3 * a] * Rv[1] + o[6 + 3 * a] * Rv[2];
                             RQR += Rv[a] * QR[a];
                         }
                         double r3 = r2 * r, r5 = r3 * r2, r7 = r5 * r2;
@@ -230,6 +255,8 @@ void nf_oracle_cutoff(int64_t cpd, double w, double eps, int64_t n_min,
         acc[3 * s + 1] = ay;
         acc[3 * s + 2] = az;
     }
+    free(mom);
+    free(slot);
 }
 
 /*

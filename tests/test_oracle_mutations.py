@@ -55,8 +55,7 @@ MUTANTS = [
     ("cutoff radial quadrupole factor", "2.5 * RQR * Rv[1] / r7", "1.5 * RQR * Rv[1] / r7", CUT_PINS),
     ("cutoff quadrupole trace", "3.0 * sv[a] * sv[bb] - (a == bb ? s2 : 0.0)", "3.0 * sv[a] * sv[bb]", CUT_PINS),
     ("cutoff centre of mass", "X[a] /= m;", "X[a] /= m + 1.0;", CUT_PINS),
-    ("cutoff sub-cell binning", "floor((xrel[3 * j + a] + 0.5) * CUT_K)", "floor((xrel[3 * j + a] + 0.5) * (CUT_K - 1))",
-     CUT_PINS),
+    ("cutoff sub-cell binning", "floor((x[a] + 0.5) * CUT_K)", "floor((x[a] + 0.5) * (CUT_K - 1))", CUT_PINS),
     ("cutoff near layer", "int far = abs(dx) == 2 || abs(dy) == 2 || abs(dz) == 2;",
      "int far = abs(dx) >= 1 || abs(dy) >= 1 || abs(dz) >= 1;", CUT_PINS),
 ]
