@@ -462,6 +462,47 @@ def run_adjoint(args):
     return 0
 
 
+def run_cutoff(args):
+    """Secondary measurement: the cut-off mode (dense far cells through sub-cell quadrupoles) on the 512^3
+    workload against the exact pass, with both compared to the FP64 oracles on sampled sinks."""
+    import torch
+    import oracle
+    import paper_1810_02916_b300 as nfb
+    w = _make_workload(WORKLOAD)
+    nf = nfb.NearField(w.cpd, w.eps, w.box)
+    nf.bin_particles(torch.from_numpy(w.pos).cuda())
+    acc = torch.empty((nf.n, 4), device="cuda")
+    exact_pairs = nf.pair_count()
+    out = dict(mode="cutoff", workload=WORKLOAD, particles=nf.n, exact_pairs=exact_pairs, n_min=args.cutoff)
+    results = {}
+    for name, n_min in (("exact", 0), ("cutoff", args.cutoff)):
+        nf.set_cutoff(n_min)
+        for _ in range(args.warmup):
+            nf.forces(acc)
+        nf.profile(True)
+        for _ in range(args.steps):
+            nf.forces(acc)
+        k, ms = nf.profile_read()
+        nf.profile(False)
+        results[name] = acc[:, :3].cpu().numpy().astype(np.float64)
+        out[name] = dict(ms=ms / k, exact_pairs_per_s=exact_pairs / (ms / k * 1e-3) / 1e9,
+                         direct_pairs=nf.pair_count())
+    out["speedup"] = out["exact"]["ms"] / out["cutoff"]["ms"]
+    b = oracle.bin_positions(w.pos, w.cpd, w.box)
+    rng = np.random.default_rng(11)
+    sinks = np.sort(rng.choice(b.n, 4000, replace=False)).astype(np.int64)
+    ex = oracle.forces(b, w.eps, sinks)
+    cu = oracle.cutoff(b, w.eps, args.cutoff, sinks)
+    out["cutoff"]["error_vs_cutoff_oracle"] = oracle.error_stats(results["cutoff"][sinks], cu)
+    out["cutoff"]["error_vs_exact_oracle"] = oracle.error_stats(results["cutoff"][sinks], ex)
+    out["cutoff_oracle_vs_exact_oracle"] = oracle.error_stats(cu, ex)
+    out["exact"]["error_vs_exact_oracle"] = oracle.error_stats(results["exact"][sinks], ex)
+    out["unit"] = "Gpair/s (exact pairs / time)"
+    nf.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_multipoles(args):
     """Secondary measurement: order-8 Cartesian multipoles of every cell of the 256^3 clustered box."""
     import torch
@@ -500,8 +541,9 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--workload", default=WORKLOAD, help="profiling driver only (with --forces-only)")
     ap.add_argument("--forces-only", type=int, default=0, help="profiling driver: this many force passes")
+    ap.add_argument("--cutoff", type=int, default=1024, help="--mode cutoff: n_min of the dense far cells")
     ap.add_argument("--plain", action="store_true", help="profiling driver: plain FP32 accumulation")
-    ap.add_argument("--mode", default="step", choices=["step", "batched", "adjoint", "multipoles"],
+    ap.add_argument("--mode", default="step", choices=["step", "batched", "adjoint", "multipoles", "cutoff"],
                     help="batched / adjoint: secondary measurements (not the bench line)")
     args = ap.parse_args()
     if args.mode == "batched":
@@ -510,6 +552,8 @@ def main():
         return run_adjoint(args)
     if args.mode == "multipoles":
         return run_multipoles(args)
+    if args.mode == "cutoff":
+        return run_cutoff(args)
     if args.forces_only:
         return run_forces_only(args)
     if args.impl == "reference":

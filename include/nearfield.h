@@ -107,6 +107,25 @@ int nf_set_accumulation(nf_t *nf, int mode);
  */
 int nf_set_softening(nf_t *nf, int mode);
 
+/*
+ * nf_set_cutoff -- cut-off acceleration of dense cells for later nf_forces
+ * calls (the paper leaves trees for dense clusters to future versions, with
+ * the opening rule set by the efficiency-accuracy trade-off, Section 2.1; this
+ * is one such trade-off, an approximation that changes the results).
+ * n_min = 0 (default): the exact near field.  n_min >= 1024: a cell at
+ * Chebyshev distance 2 from the sink's cell holding at least n_min particles
+ * acts through the quadrupole expansions of its 4^3 sub-cells about their
+ * centres of mass (a particle's sub-cell along an axis is
+ * floor((x_rel + 1/2) 4)); the 27 near cells and sparser far cells are summed
+ * pair by pair as before.  The sub-cell moments are recomputed from the
+ * current positions by every nf_forces call.  nf_pair_count then counts the
+ * pairs summed directly.
+ * Errors: NF_EINVAL for 0 < n_min < 1024; NF_ESTATE with Plummer softening.
+ * The adjoint (nf_vjp) and nf_forces_batched stay exact-only and refuse a
+ * box in cut-off mode with NF_ESTATE / NF_EINVAL.
+ */
+int nf_set_cutoff(nf_t *nf, int64_t n_min);
+
 /* nf_spline_eps_from_plummer -- the spline length with the same minimum
  * pairwise dynamical time as a Plummer length: eps_s = 2.16 eps_p
  * (Section 4.3.1). */

@@ -29,7 +29,7 @@ EXPORTS = [
     "nf_set_particles", "nf_set_velocities", "nf_get_particles", "nf_num_particles", "nf_pair_count", "nf_forces",
     "nf_get_forces64", "nf_kick_drift", "nf_vjp", "nf_forces_batched", "nf_profile", "nf_profile_read",
     "nf_set_shape", "nf_tune", "nf_forces_noalloc", "nf_set_softening", "nf_spline_eps_from_plummer",
-    "nf_choose_dt", "nf_multipoles",
+    "nf_choose_dt", "nf_multipoles", "nf_set_cutoff",
 ]
 
 
@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
             "nf_tune": ([p, ctypes.c_char_p, i], i),
             "nf_forces_noalloc": ([i, d, d, p, p, i64, p, p, ctypes.c_char_p, i], i),
             "nf_set_softening": ([p, i], i),
+            "nf_set_cutoff": ([p, ctypes.c_int64], i),
             "nf_choose_dt": ([p, d, d, ctypes.POINTER(d), ctypes.POINTER(d)], i),
             "nf_multipoles": ([p, i, p], i),
             "nf_spline_eps_from_plummer": ([d], d),
@@ -170,6 +171,11 @@ class NearField:
     def set_softening(self, mode: int):
         """SPLINE (compact spline, eps = eps_s) or PLUMMER (eps = eps_p)."""
         self._call("nf_set_softening", int(mode))
+
+    def set_cutoff(self, n_min: int):
+        """0: exact near field; >= 1024: far cells of >= n_min particles act through
+        the quadrupoles of their 4^3 sub-cells (an approximation; see nf_set_cutoff)."""
+        self._call("nf_set_cutoff", int(n_min))
 
     # -------------------------------------------------------------- particles
     def bin_particles(self, xyz):

@@ -68,6 +68,10 @@ struct nf_box {
     int *split_k = nullptr, *split_p = nullptr, *split_r = nullptr;
     void *split_scan = nullptr;
     int *nbr = nullptr;               // sources in each cell's neighbourhood
+    // cut-off mode (dense far cells through sub-cell moments); cut_nmin = 0: exact
+    int64_t cut_nmin = 0, dense_cap = 0;
+    int *dslot = nullptr, *dense_cells = nullptr, *n_dense = nullptr;
+    float *mpole = nullptr;
     const int **nbr_ptr = nullptr;    // device copy of nbr's address (the split planner reads boxes' tables)
     long long wf = 0;                 // resident warps (<= 32 per SM) x balance factor 4
     int reduce_cap = 0;
@@ -279,6 +283,8 @@ void fill_box_desc(nf_t *nf, BoxDev &b, float4 *acc_out, double *acc64, const fl
     b.eps2 = static_cast<float>(ec * ec);
     b.acc_scale = nf->inv_w * nf->inv_w;
     b.grad_scale = nf->inv_w * nf->inv_w * nf->inv_w;
+    b.dslot = nf->cut_nmin > 0 ? nf->dslot : nullptr;
+    b.mpole = nf->cut_nmin > 0 ? nf->mpole : nullptr;
 }
 
 int upload_box(nf_t *nf, float4 *acc_out, double *acc64, const float4 *cot)
@@ -293,12 +299,33 @@ int upload_box(nf_t *nf, float4 *acc_out, double *acc64, const float4 *cot)
     return NF_OK;
 }
 
+// cut-off mode buffers: slots for every cell, moments for up to n / n_min dense cells
+int ensure_cutoff(nf_t *nf)
+{
+    int rc = NF_OK;
+    if (!nf->dslot && ((rc = dalloc(nf, &nf->dslot, sizeof(int) * (static_cast<size_t>(nf->ncell) + 1))) ||
+                       (rc = dalloc(nf, &nf->n_dense, sizeof(int) * 4))))
+        return rc;
+    const int64_t need = nf->n / nf->cut_nmin + 1;
+    if (need <= nf->dense_cap) return NF_OK;
+    NF_CK(cudaStreamSynchronize(nf->stream));
+    dfree(nf->dense_cells);
+    dfree(nf->mpole);
+    nf->dense_cap = 0;
+    if ((rc = dalloc(nf, &nf->dense_cells, sizeof(int) * static_cast<size_t>(need))) ||
+        (rc = dalloc(nf, &nf->mpole, sizeof(float) * nf::kCutSub * nf::kCutWords * static_cast<size_t>(need))))
+        return rc;
+    nf->dense_cap = need;
+    return NF_OK;
+}
+
 // items of this box (all classes, largest first) into nf->items
 int plan(nf_t *nf)
 {
     // neighbourhood sizes and the pass's pair count, the items (occupancy classes, then
     // lane items), then the source split
-    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->pairs, nf->counts, nf->nbr, nf->stream));
+    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->cut_nmin, nf->pairs, nf->counts, nf->offsets, nf->nbr,
+                              nf->stream));
     NF_CK(nf::zero_device_int(nf->n_raw, nf->stream));
     for (int cls = 0; cls < nf::kClasses; ++cls)
         NF_CK(nf::plan_items_class(nf->cell_start, nf->nbr, nf->ncell, 0, cls, nf->items_raw, nf->n_raw, nf->counts,
@@ -308,6 +335,12 @@ int plan(nf_t *nf)
     NF_CK(nf::split_items(nf->items_raw, nf->n_raw, static_cast<int>(nf->item_cap), nf->nbr_ptr, nf->pairs, nf->wf,
                           kSplitFloor, nf->split_k, nf->split_p, nf->split_r, nf->split_scan, nf->items,
                           nf->n_items, nf->pieces, nf->reduces, nf->n_reduce, nf->stream));
+    if (nf->cut_nmin > 0) {
+        int rc = ensure_cutoff(nf);
+        if (rc) return rc;
+        NF_CK(nf::plan_dense_cells(nf->cell_start, nf->ncell, nf->cut_nmin, nf->dslot, nf->dense_cells, nf->n_dense,
+                                   nf->counts, nf->offsets, nf->scan_tmp, nf->stream));
+    }
     return NF_OK;
 }
 
@@ -353,6 +386,9 @@ int launch_forces(nf_t *nf, const BoxDev *d_boxes, const Item *items, const int 
         nf->ev_used += 2;
         NF_CK(cudaEventRecord(e0, nf->stream));
     }
+    if (!adjoint && nf->cut_nmin > 0 && d_boxes == nf->d_box)
+        NF_CK(nf::subcell_moments(nf->cell_start, nf->pos, nf->dense_cells, nf->n_dense, nf->dense_cap, nf->mpole,
+                                  nf->sm_count, nf->stream));
     NF_CK(nf::launch_pair(d_boxes, items, n_items, queue, nf->acc_mode == NF_ACC_COMPENSATED, adjoint, nf->softening,
                           nf->shape,
                           nf->sm_count, nf->stream));
@@ -523,6 +559,7 @@ void nf_destroy(nf_t *nf)
     cudaStreamSynchronize(nf->stream);
     free_particles(nf);
     dfree(nf->cell_start); dfree(nf->counts); dfree(nf->offsets); dfree(nf->nbr);
+    dfree(nf->dslot); dfree(nf->dense_cells); dfree(nf->n_dense); dfree(nf->mpole);
     if (nf->scan_tmp) cudaFree(nf->scan_tmp);
     dfree(nf->n_items); dfree(nf->queue); dfree(nf->err); dfree(nf->pairs); dfree(nf->d_box);
     dfree(nf->n_raw); dfree(nf->n_reduce); dfree(nf->nbr_ptr);
@@ -557,7 +594,27 @@ int nf_set_softening(nf_t *nf, int mode)
 {
     if (!nf) return NF_EINVAL;
     if (mode != NF_SPLINE && mode != NF_PLUMMER) return fail(nf, NF_EINVAL, "unknown softening mode");
+    if (mode != NF_SPLINE && nf->cut_nmin > 0)
+        return fail(nf, NF_ESTATE, "the cut-off mode applies to the spline law only; set it to 0 first");
     nf->softening = mode;
+    return NF_OK;
+}
+
+int nf_set_cutoff(nf_t *nf, int64_t n_min)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (n_min < 0 || (n_min > 0 && n_min < nf::kCutMinN))
+        return fail(nf, NF_EINVAL, "n_min must be 0 (exact) or at least " + std::to_string(nf::kCutMinN));
+    if (n_min > 0 && nf->softening != NF_SPLINE)
+        return fail(nf, NF_ESTATE, "the cut-off mode applies to the spline law only");
+    if (n_min == nf->cut_nmin) return NF_OK;
+    nf->cut_nmin = n_min;
+    nf->box_dirty = true;
+    if (nf->have_particles) {
+        if ((rc = plan(nf))) return rc;
+        NF_CK(cudaStreamSynchronize(nf->stream));
+    }
     return NF_OK;
 }
 
@@ -709,7 +766,8 @@ int nf_pair_count(nf_t *nf, int64_t *pairs)
     if (rc) return rc;
     if (!pairs) return fail(nf, NF_EINVAL, "pairs is NULL");
     if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
-    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->pairs, nf->counts, nf->nbr, nf->stream));
+    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->cut_nmin, nf->pairs, nf->counts, nf->offsets, nf->nbr,
+                              nf->stream));
     unsigned long long h = 0;
     NF_CK(cudaMemcpyAsync(&h, nf->pairs, sizeof(h), cudaMemcpyDeviceToHost, nf->stream));
     NF_CK(cudaStreamSynchronize(nf->stream));
@@ -761,6 +819,7 @@ int nf_vjp(nf_t *nf, const float *w, float *grad)
     int rc = check_box(nf);
     if (rc) return rc;
     if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
+    if (nf->cut_nmin > 0) return fail(nf, NF_ESTATE, "the adjoint is exact-only; set the cut-off to 0 first");
     if (nf->n == 0) return NF_OK;
     if (!w || !grad) return fail(nf, NF_EINVAL, "NULL input");
     const size_t bytes = sizeof(float4) * static_cast<size_t>(nf->n);
@@ -1060,6 +1119,7 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
         if (!boxes[b]->have_particles) return fail(nf, NF_ESTATE, "box without particles");
         if (boxes[b]->device != nf->device) return fail(nf, NF_EINVAL, "boxes on different devices");
         if (boxes[b]->softening != nf->softening) return fail(nf, NF_EINVAL, "boxes with different softening");
+        if (boxes[b]->cut_nmin > 0) return fail(nf, NF_EINVAL, "the batched launch is exact-only (a box has a cut-off)");
     }
     std::lock_guard<std::mutex> lk(g_batch_mu);
     Batch &B = g_batch;
@@ -1080,7 +1140,7 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
         std::vector<const unsigned long long *> prs(nbox);
         for (int b = 0; b < nbox; ++b) {
             nf_t *x = boxes[b];
-            NF_CK(nf::neighbour_pairs(x->cell_start, x->cpd, x->pairs, x->counts, x->nbr, nf->stream));
+            NF_CK(nf::neighbour_pairs(x->cell_start, x->cpd, 0, x->pairs, x->counts, x->offsets, x->nbr, nf->stream));
             nbr[b] = x->nbr;
             prs[b] = x->pairs;
         }

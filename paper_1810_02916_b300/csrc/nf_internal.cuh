@@ -37,6 +37,8 @@ struct BoxDev {
     float eps2;               // eps^2 in cell units (spline: adjoint branch test; Plummer: eps_p^2)
     double acc_scale;         // (cpd / box)^2: cell-unit acceleration -> box units
     double grad_scale;        // (cpd / box)^3: cell-unit Jacobian -> box units
+    const int *dslot;         // cut-off mode: moment slot of each dense cell, -1 elsewhere (null: exact mode)
+    const float *mpole;       // cut-off mode: kCutWords floats per sub-cell, kCutSub sub-cells per dense cell
 };
 
 // A work item: up to kTile sinks of one cell against its neighbourhood (or a
@@ -77,6 +79,15 @@ struct Reduce {
     int slot;
     int pieces;
 };
+
+// Cut-off acceleration of dense cells: a far cell (Chebyshev distance 2) of
+// at least n_min particles acts through the quadrupoles of its kCutK^3
+// sub-cells.  Per sub-cell: count, centre of mass (cell units, the cell's own
+// frame), traceless Q_xx, Q_xy, Q_xz, Q_yy, Q_yz, Q_zz (cell units^2).
+constexpr int kCutK = 4;
+constexpr int kCutSub = kCutK * kCutK * kCutK;
+constexpr int kCutWords = 10;
+constexpr int kCutMinN = 1024;   // smallest n_min: dense cells never border lane items (<= kLaneMaxT sources)
 
 // Occupancy classes used to order the work queue (largest cells first).
 constexpr int kClasses = 5;
@@ -140,10 +151,17 @@ cudaError_t split_items(const Item *items_in, const int *n_in, int item_cap, con
 cudaError_t sum_pair_counts(const unsigned long long *const *ptrs, int n, unsigned long long *out, cudaStream_t st);
 cudaError_t reduce_partials(const BoxDev *boxes, const Reduce *reduces, const int *n_reduce, int max_reduce,
                             int adjoint, cudaStream_t st);
-// sources in each cell's 125-cell neighbourhood into nbr (ncell ints; tmp:
-// ncell ints of scratch) and the pass's pair count sum_c n_c nbr_c into *pairs
-cudaError_t neighbour_pairs(const int *cell_start, int cpd, unsigned long long *pairs, int *tmp, int *nbr,
-                            cudaStream_t st);
+// sources summed directly in each cell's 125-cell neighbourhood into nbr
+// (ncell ints; tmp, tmp2: ncell ints of scratch) and the pass's pair count
+// sum_c n_c nbr_c into *pairs.  With n_min > 0 (cut-off mode) far cells of at
+// least n_min particles are left out (they act through sub-cell moments).
+cudaError_t neighbour_pairs(const int *cell_start, int cpd, int64_t n_min, unsigned long long *pairs, int *tmp,
+                            int *tmp2, int *nbr, cudaStream_t st);
+// cut-off mode: dslot[c] = rank of cell c among the cells of >= n_min particles
+// (-1 for the others), dense_cells[rank] = c, *n_dense = their number.
+cudaError_t plan_dense_cells(const int *cell_start, int ncell, int64_t n_min, int *dslot, int *dense_cells,
+                             int *n_dense, int *scratch_counts, int *scratch_offsets, void *scan_temp,
+                             cudaStream_t st);
 
 // ---- kick / drift (nf_step.cu) ----
 // kick + drift of every particle into particle-id order (xq_by_id.w holds the
@@ -155,6 +173,9 @@ cudaError_t kick_drift(const float4 *pos, const float4 *vel, const double *acc64
 cudaError_t drift_keys(const float4 *xq_by_id, int n, uint32_t *keys, uint32_t *vals, int *counts, cudaStream_t st);
 
 // cell multipoles (nf_multipole.cu)
+// cut-off mode: the sub-cell moments of the dense cells (mpole, kCutSub * kCutWords floats per dense cell)
+cudaError_t subcell_moments(const int *cell_start, const float4 *pos, const int *dense_cells, const int *n_dense,
+                            int64_t dense_cap, float *mpole, int sm_count, cudaStream_t st);
 int multipole_terms(int order);
 cudaError_t cell_multipoles(const int *cell_start, int ncell, const float4 *pos, int order, double *out, int sm_count,
                             cudaStream_t st);

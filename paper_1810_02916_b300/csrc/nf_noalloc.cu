@@ -153,7 +153,7 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     if (n == 0) return NF_OK;
 
     // work list (items ordered largest cells first), then the descriptor, then the pair kernel
-    NA_CK(nf::neighbour_pairs(cell_start, cpd, pairs, counts, nbr, st));
+    NA_CK(nf::neighbour_pairs(cell_start, cpd, 0, pairs, counts, offsets, nbr, st));
     NA_CK(nf::zero_device_int(n_items, st));
     for (int cls = 0; cls < nf::kClasses; ++cls)
         NA_CK(nf::plan_items_class(cell_start, nbr, ncell, 0, cls, items, n_items, counts, offsets, scan_tmp, st));

@@ -259,6 +259,27 @@ __device__ __forceinline__ void pair_force2_far(const float2 qx, const float2 qy
     tail2_newton(dx, dy, dz, __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx))), ax, ay, az);
 }
 
+// Acceleration from a sub-cell's quadrupole expansion about its centre of mass
+// (cut-off mode): R = centre - sink, sum_j 1/|R + s_j| = M/r + (R.Q.R)/(2 r^5)
+// + O(s^3), so a += M R/r^3 - Q R/r^5 + (5/2)(R.Q.R) R/r^7 (Newtonian: the
+// sub-cell lies beyond eps).  q = Q_xx, Q_xy, Q_xz, Q_yy, Q_yz, Q_zz.
+__device__ __forceinline__ void quad_force(float rx, float ry, float rz, float M, const float *q, float &ax,
+                                           float &ay, float &az)
+{
+    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+    float y = rsqrtf(r2);
+    y = y * fmaf(-0.5f * r2, y * y, 1.5f);   // one Newton step
+    const float y2 = y * y, y3 = y2 * y, y5 = y3 * y2, y7 = y5 * y2;
+    const float qx = fmaf(q[2], rz, fmaf(q[1], ry, q[0] * rx));
+    const float qy = fmaf(q[4], rz, fmaf(q[3], ry, q[1] * rx));
+    const float qz = fmaf(q[5], rz, fmaf(q[4], ry, q[2] * rx));
+    const float rqr = fmaf(rz, qz, fmaf(ry, qy, rx * qx));
+    const float c = fmaf(2.5f * rqr, y7, M * y3);
+    ax = fmaf(c, rx, fmaf(-y5, qx, ax));
+    ay = fmaf(c, ry, fmaf(-y5, qy, ay));
+    az = fmaf(c, rz, fmaf(-y5, qz, az));
+}
+
 // one pair of the adjoint: grad += J(d) (w_j - w_k), J = f I + (f'/r) d d^T
 template <int SOFT>
 __device__ __forceinline__ void pair_adjoint(const float4 q, const float4 wj, float xi, float yi, float zi, float wx,
@@ -343,8 +364,17 @@ __device__ __forceinline__ int build_table(const BoxDev &bx, int cell, int *tsta
             ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
             nz += nz < 0 ? C : 0; nz -= nz >= C ? C : 0;
             const int n = (nx * C + ny) * C + nz;
-            const int s0 = __ldg(bx.cell_start + n);
+            int s0 = __ldg(bx.cell_start + n);
             c = __ldg(bx.cell_start + n + 1) - s0;
+            if (bx.dslot != nullptr && p >= kNear) {
+                // cut-off mode: a dense far cell acts through its sub-cell moments, not
+                // pair by pair; its entry holds -2 - (moment slot) and no sources
+                const int ds = __ldg(bx.dslot + n);
+                if (ds >= 0) {
+                    c = 0;
+                    s0 = -2 - ds;
+                }
+            }
             tstart[p] = s0;
         }
         cnt[u] = c;
@@ -732,6 +762,53 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
             px[2 * k] = ax2[k].x; py[2 * k] = ay2[k].x; pz[2 * k] = az2[k].x;
             px[2 * k + 1] = ax2[k].y; py[2 * k + 1] = ay2[k].y; pz[2 * k + 1] = az2[k].y;
         }
+    }
+    // cut-off mode: the dense far cells, once per item (by its first source piece)
+    if (SOFT == 0 && !ADJ && bx.mpole != nullptr &&
+        (item.piece < 0 || __ldg(&bx.pieces[item.piece].src_lo) == 0)) {
+        float sxp[SS], syp[SS], szp[SS], mx[SS], my[SS], mz[SS];
+#pragma unroll
+        for (int s = 0; s < SS; ++s) {
+            const int k = SPLIT ? (lane & (P - 1)) : lane + 32 * s;
+            const float4 p = __ldg(bx.pos + item.sink_begin + min(k, count - 1));
+            sxp[s] = p.x; syp[s] = p.y; szp[s] = p.z;
+            mx[s] = my[s] = mz[s] = 0.f;
+        }
+        // in split mode the sub-cells are shared out over the lane groups, whose sums
+        // the xor tree below adds, so each sub-cell counts once
+        const int q0 = SPLIT ? my_split : 0, dq = SPLIT ? splits : 1;
+        float *moments = reinterpret_cast<float *>(stage);   // free once the last round is done
+        for (int pp = kNear; pp < kNbr; ++pp) {
+            const int ts = tstart[pp];
+            if (ts > -2) continue;
+            const float4 *src = reinterpret_cast<const float4 *>(bx.mpole) +
+                                static_cast<int64_t>(-2 - ts) * (kCutSub * kCutWords / 4);
+            __syncwarp();
+            for (int k = lane; k < kCutSub * kCutWords / 4; k += 32) stage[k] = __ldg(src + k);
+            __syncwarp();
+            const int t = __ldg(&kNbrOrder.code[pp]);
+            const float ox = static_cast<float>(t / 25 - 2), oy = static_cast<float>((t / 5) % 5 - 2),
+                        oz = static_cast<float>(t % 5 - 2);
+            for (int q = q0; q < kCutSub; q += dq) {
+                const float *o = moments + q * kCutWords;
+                const float M = o[0];
+                if (M == 0.f) continue;
+                const float cx = o[1] + ox, cy = o[2] + oy, cz = o[3] + oz;
+#pragma unroll
+                for (int s = 0; s < SS; ++s) quad_force(cx - sxp[s], cy - syp[s], cz - szp[s], M, o + 4, mx[s], my[s], mz[s]);
+            }
+            // one FP32 partial per dense cell, folded like a round of sources
+#pragma unroll
+            for (int s = 0; s < SS; ++s) {
+                if (COMP) {
+                    comp_fold_smem(comp + lane + 32 * s, mx[s], my[s], mz[s]);
+                } else {
+                    px[s] += mx[s]; py[s] += my[s]; pz[s] += mz[s];
+                    mx[s] = my[s] = mz[s] = 0.f;
+                }
+            }
+        }
+        __syncwarp();
     }
     Comp3 acc[SS];
 #pragma unroll

@@ -158,8 +158,8 @@ __global__ void advance_base(int *__restrict__ base_p, const int *__restrict__ o
 
 __global__ void zero_int(int *p) { *p = 0; }
 
-// 5-point periodic window sum along one axis of a cpd^3 array
-__global__ void window_sum(const int *__restrict__ in, int *__restrict__ out, int cpd, int axis)
+// (2 radius + 1)-point periodic window sum along one axis of a cpd^3 array
+__global__ void window_sum(const int *__restrict__ in, int *__restrict__ out, int cpd, int axis, int radius)
 {
     const int64_t ncell = static_cast<int64_t>(cpd) * cpd * cpd;
     const int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -167,7 +167,7 @@ __global__ void window_sum(const int *__restrict__ in, int *__restrict__ out, in
     const int z = static_cast<int>(c % cpd), y = static_cast<int>((c / cpd) % cpd);
     const int x = static_cast<int>(c / (static_cast<int64_t>(cpd) * cpd));
     int s = 0;
-    for (int d = -kR; d <= kR; ++d) {
+    for (int d = -radius; d <= radius; ++d) {
         int xx = x, yy = y, zz = z;
         if (axis == 0) xx = (x + d + cpd) % cpd;
         else if (axis == 1) yy = (y + d + cpd) % cpd;
@@ -177,10 +177,40 @@ __global__ void window_sum(const int *__restrict__ in, int *__restrict__ out, in
     out[c] = s;
 }
 
-__global__ void occupancy(const int *__restrict__ cell_start, int ncell, int *__restrict__ occ)
+// occupancy of every cell; with n_min > 0 only the cells below n_min (dense = 0)
+// or only those at or above it (dense = 1), zero elsewhere
+__global__ void occupancy(const int *__restrict__ cell_start, int ncell, int64_t n_min, int dense,
+                          int *__restrict__ occ)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < ncell) occ[c] = cell_start[c + 1] - cell_start[c];
+    if (c >= ncell) return;
+    const int n = cell_start[c + 1] - cell_start[c];
+    occ[c] = (n_min <= 0 || (n >= n_min) == (dense != 0)) ? n : 0;
+}
+
+__global__ void add_into(int *__restrict__ a, const int *__restrict__ b, int ncell)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) a[c] += b[c];
+}
+
+__global__ void dense_flags(const int *__restrict__ cell_start, int ncell, int64_t n_min, int *__restrict__ flags)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ncell) return;
+    flags[c] = c < ncell && cell_start[c + 1] - cell_start[c] >= n_min;
+}
+
+__global__ void dense_slots(const int *__restrict__ cell_start, int ncell, int64_t n_min,
+                            const int *__restrict__ rank, int *__restrict__ dslot, int *__restrict__ dense_cells,
+                            int *__restrict__ n_dense)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) *n_dense = rank[ncell];
+    if (c >= ncell) return;
+    const bool dense = cell_start[c + 1] - cell_start[c] >= n_min;
+    dslot[c] = dense ? rank[c] : -1;
+    if (dense) dense_cells[rank[c]] = c;
 }
 
 __global__ void dot_counts(const int *__restrict__ cell_start, const int *__restrict__ nbr, int ncell,
@@ -372,6 +402,20 @@ cudaError_t plan_items_class(const int *cell_start, const int *nbr, int ncell, i
     return cudaGetLastError();
 }
 
+cudaError_t plan_dense_cells(const int *cell_start, int ncell, int64_t n_min, int *dslot, int *dense_cells,
+                             int *n_dense, int *scratch_counts, int *scratch_offsets, void *scan_temp,
+                             cudaStream_t st)
+{
+    dense_flags<<<nblocks(static_cast<int64_t>(ncell) + 1, 256), 256, 0, st>>>(cell_start, ncell, n_min,
+                                                                                scratch_counts);
+    cudaError_t e =
+        exclusive_scan_i32(scratch_counts, scratch_offsets, static_cast<int64_t>(ncell) + 1, scan_temp, st);
+    if (e != cudaSuccess) return e;
+    dense_slots<<<nblocks(ncell > 0 ? ncell : 1, 256), 256, 0, st>>>(cell_start, ncell, n_min, scratch_offsets, dslot,
+                                                                      dense_cells, n_dense);
+    return cudaGetLastError();
+}
+
 cudaError_t plan_lane_items(const int *cell_start, const int *nbr, int cpd, int box_index, Item *items, int *n_items,
                             int *scratch_counts, int *scratch_offsets, void *scan_temp, cudaStream_t st)
 {
@@ -385,14 +429,23 @@ cudaError_t plan_lane_items(const int *cell_start, const int *nbr, int cpd, int 
     return cudaGetLastError();
 }
 
-cudaError_t neighbour_pairs(const int *cell_start, int cpd, unsigned long long *pairs, int *tmp, int *nbr,
-                            cudaStream_t st)
+cudaError_t neighbour_pairs(const int *cell_start, int cpd, int64_t n_min, unsigned long long *pairs, int *tmp,
+                            int *tmp2, int *nbr, cudaStream_t st)
 {
     const int ncell = cpd * cpd * cpd;
-    occupancy<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, tmp);
-    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr, cpd, 2);
-    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(nbr, tmp, cpd, 1);
-    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr, cpd, 0);
+    // cells summed over the whole 125-cell window (all of them, or those below n_min) ...
+    occupancy<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, n_min, 0, tmp);
+    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr, cpd, 2, kR);
+    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(nbr, tmp, cpd, 1, kR);
+    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr, cpd, 0, kR);
+    if (n_min > 0) {
+        // ... and, in cut-off mode, the dense cells over the 27 near cells only
+        occupancy<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, n_min, 1, tmp);
+        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, tmp2, cpd, 2, 1);
+        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp2, tmp, cpd, 1, 1);
+        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, tmp2, cpd, 0, 1);
+        add_into<<<nblocks(ncell, 256), 256, 0, st>>>(nbr, tmp2, ncell);
+    }
     cudaMemsetAsync(pairs, 0, sizeof(unsigned long long), st);
     dot_counts<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, nbr, ncell, pairs);
     return cudaGetLastError();

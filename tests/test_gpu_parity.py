@@ -364,3 +364,75 @@ def test_lane_items_mixed_occupancy():
     acc = nf.forces()
     ref, sa, _ = oracle.forces(b, eps, soft=oracle.PLUMMER, with_sumabs=True)
     _check_forces(acc, ref, sa)
+
+
+
+# ------------------------------------------------------------------ cut-off acceleration of dense cells
+
+def _dense_box():
+    rng = np.random.default_rng(51)
+    X, _ = gen.clustered(200000, rng, 6, 0.3 / 16, 1.2 / 16)
+    return X, 16, 0.01 / 16
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["compensated", "plain"])
+def test_cutoff_matches_its_oracle(mode):
+    """Dense far cells through sub-cell quadrupoles: parity with the FP64 oracle of the same
+    approximation, the approximation's own error against the exact sum, fewer direct pairs,
+    and the exact pass back once the cut-off is 0."""
+    X, cpd, eps = _dense_box()
+    nf = make_box(X, cpd, eps, mode=mode)
+    b = oracle_side(X, cpd)
+    assert int((b.counts >= 1024).sum()) >= 10
+    exact = nf.forces()
+    exact_pairs = nf.pair_count()
+    nf.set_cutoff(1024)
+    acc = nf.forces()
+    assert nf.pair_count() < exact_pairs
+    sinks = sample_sinks(b, 20000)
+    ref = oracle.cutoff(b, eps, 1024, sinks)
+    s = oracle.error_stats(acc[sinks, :3], ref)
+    assert s["rms_rel"] <= (RMS_TOL if mode == 0 else RMS_TOL_PLAIN), s
+    s_exact = oracle.error_stats(acc[sinks, :3], oracle.forces(b, eps, sinks=sinks))
+    assert s_exact["rms_rel"] <= 1e-4, s_exact
+    assert not np.array_equal(acc, exact)
+    nf.set_cutoff(0)
+    assert np.array_equal(nf.forces(), exact)
+
+
+def test_cutoff_without_dense_cells_is_the_exact_pass():
+    X, cpd, eps = _dense_box()
+    nf = make_box(X, cpd, eps)
+    exact = nf.forces()
+    nf.set_cutoff(1 << 40)
+    assert np.array_equal(nf.forces(), exact)
+
+
+def test_cutoff_follows_kick_drift_and_refuses_exact_only_calls():
+    import paper_1810_02916_b300 as nfb
+    X, cpd, eps = _dense_box()
+    nf = make_box(X, cpd, eps)
+    with pytest.raises(nfb.NearFieldError) as e:
+        nf.set_cutoff(100)
+    assert e.value.code == nfb.NF_EINVAL
+    nf.set_cutoff(1024)
+    with pytest.raises(nfb.NearFieldError) as e:
+        nf.set_softening(nfb.PLUMMER)
+    assert e.value.code == nfb.NF_ESTATE
+    W = np.zeros((nf.n, 4), np.float32)
+    with pytest.raises(nfb.NearFieldError) as e:
+        nf.vjp(W)
+    assert e.value.code == nfb.NF_ESTATE
+    with pytest.raises(nfb.NearFieldError) as e:
+        nfb.forces_batched([nf])
+    assert e.value.code == nfb.NF_EINVAL
+    # a step re-plans the dense cells from the drifted particles
+    acc = nf.forces()
+    amax = float(np.abs(acc[:, :3]).max())
+    nf.kick_drift(0.2 * np.sqrt(eps / amax))
+    acc2 = nf.forces()
+    st = nf.get_particles()
+    b2 = oracle.from_sorted(cpd, 1.0, st["cell_offsets"], st["pos"][:, :3])   # the drifted layout as held
+    sinks = sample_sinks(b2, 5000)
+    s = oracle.error_stats(acc2[sinks, :3], oracle.cutoff(b2, eps, 1024, sinks))
+    assert s["rms_rel"] <= RMS_TOL, s
