@@ -386,6 +386,7 @@ int launch_forces(nf_t *nf, const BoxDev *d_boxes, const Item *items, const int 
         nf->ev_used += 2;
         NF_CK(cudaEventRecord(e0, nf->stream));
     }
+    // cut-off mode: this pass's sub-cell moments (inside the profiled interval)
     if (!adjoint && nf->cut_nmin > 0 && d_boxes == nf->d_box)
         NF_CK(nf::subcell_moments(nf->cell_start, nf->pos, nf->dense_cells, nf->n_dense, nf->dense_cap, nf->mpole,
                                   nf->sm_count, nf->stream));
