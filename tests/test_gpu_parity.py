@@ -436,3 +436,36 @@ def test_cutoff_follows_kick_drift_and_refuses_exact_only_calls():
     sinks = sample_sinks(b2, 5000)
     s = oracle.error_stats(acc2[sinks, :3], oracle.cutoff(b2, eps, 1024, sinks))
     assert s["rms_rel"] <= RMS_TOL, s
+
+
+def test_cutoff_with_lane_items_and_split_pieces():
+    """One particle per cell of background (lane items) around two dense halos (cut-off
+    moments, source pieces): forces against the cut-off oracle, and the direct-pair count
+    against a window sum over the cell counts (sparse cells over 5^3, dense ones over 3^3)."""
+    cpd = 30
+    rng = np.random.default_rng(61)
+    cells = np.arange(cpd ** 3)
+    base = np.stack([cells // (cpd * cpd), (cells // cpd) % cpd, cells % cpd], 1)
+    bg = (base + rng.random(base.shape)) / cpd
+    halos = [np.array([7.5, 8.5, 9.5]) / cpd + 0.6 / cpd * rng.standard_normal((9000, 3)),
+             np.array([21.5, 20.5, 3.5]) / cpd + 0.4 / cpd * rng.standard_normal((6000, 3))]
+    X = np.mod(np.concatenate([bg] + halos), 1.0)
+    eps = 0.02 / cpd
+    n_min = 1024
+    nf = make_box(X, cpd, eps)
+    nf.set_cutoff(n_min)
+    acc = nf.forces()
+    b = oracle_side(X, cpd)
+    assert int((b.counts >= n_min).sum()) >= 2 and int((b.counts <= 8).sum()) > cpd ** 3 // 2
+    sinks = sample_sinks(b, 20000)
+    s = oracle.error_stats(acc[sinks, :3], oracle.cutoff(b, eps, n_min, sinks))
+    assert s["rms_rel"] <= RMS_TOL, s
+    cnt = b.counts.reshape(cpd, cpd, cpd).astype(np.int64)
+
+    def window(a, r):
+        for ax in range(3):
+            a = sum(np.roll(a, k, axis=ax) for k in range(-r, r + 1))
+        return a
+    dense = np.where(cnt >= n_min, cnt, 0)
+    direct = int((cnt * (window(cnt - dense, 2) + window(dense, 1))).sum())
+    assert nf.pair_count() == direct
