@@ -25,8 +25,10 @@ FORCE_PINS = [
     lambda: pins.test_cells_match_bruteforce(7, 900, "clustered"),
     pins.test_third_law_total_force_vanishes,
 ]
-VJP_PINS = [lambda: pins.test_vjp_matches_central_differences(0.01),
-            lambda: pins.test_vjp_matches_central_differences(0.08)]
+VJP_PINS = [lambda: pins.test_vjp_matches_central_differences(0.01, oracle.SPLINE),
+            lambda: pins.test_vjp_matches_central_differences(0.08, oracle.SPLINE)]
+PLUMMER_VJP_PINS = [lambda: pins.test_vjp_matches_central_differences(0.01, oracle.PLUMMER),
+                    lambda: pins.test_vjp_matches_central_differences(0.08, oracle.PLUMMER)]
 CUT_PINS = [pins.test_cutoff_without_dense_cells_is_the_direct_sum,
             pins.test_cutoff_with_one_particle_per_subcell_is_exact,
             pins.test_cutoff_error_of_a_generic_cluster_falls_as_its_size_cubed,
@@ -51,6 +53,14 @@ MUTANTS = [
     ("adjoint Jacobian term", "return -3.0 / (r2 * r2 * r);", "return 3.0 / (r2 * r2 * r);", VJP_PINS),
     ("adjoint spline derivative", "(-15.0 / (eps * r) + 12.0 / (eps * eps))", "(-15.0 / (eps * r) + 6.0 / (eps * eps))",
      VJP_PINS),
+    ("Plummer force power", "return 1.0 / (s * sqrt(s));", "return 1.0 / (s * s);",
+     [pins.test_plummer_is_gradient_of_plummer_potential, pins.test_eps_conversion_matches_printed_factor]),
+    ("Plummer adjoint exponent", "return -3.0 / (s * s * sqrt(s));", "return -2.0 / (s * s * sqrt(s));",
+     PLUMMER_VJP_PINS),
+    ("Plummer adjoint power of s", "return -3.0 / (s * s * sqrt(s));", "return -3.0 / (s * sqrt(s));",
+     PLUMMER_VJP_PINS),
+    ("Plummer adjoint softening dropped", "double s = r * r + eps * eps;\n        return -3.0",
+     "double s = r * r;\n        return -3.0", PLUMMER_VJP_PINS),
     ("cutoff quadrupole sign", "ax += m * Rv[0] / r3 - QR[0] / r5", "ax += m * Rv[0] / r3 + QR[0] / r5", CUT_PINS),
     ("cutoff radial quadrupole factor", "2.5 * RQR * Rv[1] / r7", "1.5 * RQR * Rv[1] / r7", CUT_PINS),
     ("cutoff quadrupole trace", "3.0 * sv[a] * sv[bb] - (a == bb ? s2 : 0.0)", "3.0 * sv[a] * sv[bb]", CUT_PINS),

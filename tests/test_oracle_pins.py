@@ -265,15 +265,21 @@ def test_quantised_offsets_make_fp32_separations_exact():
 
 # ------------------------------------------------------------------ adjoint
 
+@pytest.mark.parametrize("soft", [oracle.SPLINE, oracle.PLUMMER], ids=["spline", "plummer"])
 @pytest.mark.parametrize("eps", [0.01, 0.08])
-def test_vjp_matches_central_differences(eps):
-    """eps = 0.08 puts most close pairs inside the spline, 0.01 most outside."""
+def test_vjp_matches_central_differences(eps, soft):
+    """Adjoint against central differences of the oracle's own forces.
+
+    Spline law: eps = 0.08 puts most close pairs inside the spline, 0.01 most
+    outside.  Plummer law (Eq. eqn:plummer, eps = eps_p): at 0.08 the softening
+    dominates the close pairs' (r^2 + eps_p^2), at 0.01 the separation does.
+    """
     rng = np.random.default_rng(13)
     cpd = 6
     X, _ = gen.clustered(800, rng, 2, 0.05, 0.15)
     b = oracle.bin_positions(X, cpd)
     wv = gen.cotangent(b.n, rng)
-    g = oracle.vjp(b, eps, wv)
+    g = oracle.vjp(b, eps, wv, soft=soft)
     x64 = b.xq.astype(np.float64)
     h = 1e-3 * eps
     for k in rng.choice(b.n, 12, replace=False):
@@ -283,7 +289,7 @@ def test_vjp_matches_central_differences(eps):
                 xp = x64.copy()
                 xp[k, ax] += sgn * h / b.w
                 bp = oracle.Binned(b.cpd, b.box, b.order, b.cell, xp, b.offsets, b.counts)
-                vals.append(float((oracle.forces(bp, eps) * wv).sum()))
+                vals.append(float((oracle.forces(bp, eps, soft=soft) * wv).sum()))
             fd = (vals[0] - vals[1]) / (2 * h)
             assert fd == pytest.approx(g[k, ax], rel=2e-5, abs=1e-6 * np.abs(g).max())
 
