@@ -45,8 +45,8 @@ FMA_OPS_PER_PAIR = 14
 BRANCH_FREE_OPS_PER_PAIR = 18   # the same with the law evaluated branch-free, min(r^-3, g(r)), for every pair
 ISSUE_OPS_PER_PAIR = 20    # FP32-pipe instructions per pair of the branch-free law issued one lane-op at a time
 # DRAM bytes (read + write) of one compensated pair-kernel launch of this workload, from the ncu
-# launch list in profiles/launches_zeldovich512_bench.md, valid while nf_pair.cu hashes to the value
-# below (the record reports null traffic once the kernel source has changed)
+# launch list of this workload, valid while nf_pair.cu hashes to the value below (the record
+# reports null traffic once the kernel source has changed)
 PAIR_TRAFFIC_BYTES = 9.3688e9
 PAIR_TRAFFIC_SOURCE_SHA256 = "486cb77da20fc0e7"
 FP32_LANES_PER_SM = 128
@@ -230,7 +230,6 @@ def run(args):
     nf.bin_particles(Xd)
     del Xd
     n = nf.n
-    pairs = nf.pair_count()
     acc_d = torch.empty((n, 4), dtype=torch.float32, device=f"cuda:{dev}")
 
     # time step: max|a| dt^2 <= 0.1 eps (so max |v| dt stays far below 0.8 cells)
@@ -255,9 +254,14 @@ def run(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    # pairs of each timed step: the count of the plan its force pass runs (read after the
+    # previous kick-drift, which has synchronised already; an 8-byte copy)
+    step_pairs = [nf.pair_count()]
     e0.record(stream)
-    for _ in range(args.steps):
+    for k in range(args.steps):
         step()
+        if k + 1 < args.steps:
+            step_pairs.append(nf.pair_count())
     e1.record(stream)
     torch.cuda.synchronize()
     nf.profile(False)
@@ -265,6 +269,7 @@ def run(args):
     clk = clocks.stop()
     launches, pair_ms = nf.profile_read()
     pair_ms /= max(launches, 1)
+    pairs = sum(step_pairs) / len(step_pairs)      # mean pairs per timed step
     t_max = max_over_ranks(step_ms, f"cuda:{dev}") if world > 1 else step_ms
     value = whole_job_rate(pairs, world, t_max)
     pair_kernel_gps = pairs / (pair_ms * 1e-3) / 1e9
@@ -277,6 +282,7 @@ def run(args):
         nf_cmp = nfb.NearField(w.cpd, w.eps, w.box)      # compare on a fresh box of the initial positions
         nf_cmp.set_stream(stream)
         nf_cmp.bin_particles(torch.from_numpy(w.pos).to(f"cuda:{dev}"))
+        pairs0 = nf_cmp.pair_count()
         acc_c = nf_cmp.forces()
         nf_cmp.set_accumulation(nfb.ACC_PLAIN)
         nf_cmp.profile(True)
@@ -292,7 +298,8 @@ def run(args):
         _, _, sampled_pairs, cpu_s, _ = _oracle_sample(w, b, kc, seed=9)
         extra = dict(
             compensated=dict(pair_kernel_gpair_s=pair_kernel_gps, error_vs_oracle=ec),
-            plain_fp32=dict(pair_kernel_gpair_s=pairs / (ms / k * 1e-3) / 1e9, error_vs_oracle=ep),
+            plain_fp32=dict(pair_kernel_gpair_s=pairs0 / (ms / k * 1e-3) / 1e9, error_vs_oracle=ep,
+                            note="initial positions of the workload, before any step"),
             cpu_baseline=dict(value=sampled_pairs / cpu_s / 1e9, unit=UNIT, cores=os.cpu_count(), kind="oracle",
                               sample=f"{kc} uniformly sampled sinks of the workload "
                                      f"({sampled_pairs} pairs, {cpu_s:.1f} s)"),
@@ -319,9 +326,14 @@ def run(args):
         torch.cuda.synchronize()
         e_s = (time.perf_counter() - t0) / args.e2e_steps
         nf_e.close()
-        e2e = dict(value=pairs / e_s / 1e9, unit=UNIT, h2d_bytes_per_step=int(xh.numel() * 8),
+        e2e = dict(value=pairs0 / e_s / 1e9, unit=UNIT, h2d_bytes_per_step=int(xh.numel() * 8),
                    d2h_bytes_per_step=int(ah.numel() * 4),
                    step="nf_bin_particles(pinned host xyz) + nf_forces(pinned host acc) + nf_kick_drift")
+
+    # secondary: the 64-box batched configuration on this GPU (one persistent launch under a CUDA graph)
+    if rank == 0 and world == 1 and args.batched_steps > 0:
+        specs = _batched_specs()
+        extra["batched"] = _time_batched(specs, list(range(len(specs))), args.batched_steps, 2)
 
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
@@ -336,7 +348,8 @@ def run(args):
             data="synthetic (seeded Zel'dovich lattice + Plummer halos)",
             config=dict(workload=f"{WORKLOAD}: N=512^3=134217728, CPD=405, R=2, eps=1/50 spacing, "
                                  "Zel'dovich P(k)~k^-1.5 + 2000 Plummer halos",
-                        pairs_per_step=pairs, particles=n, dt=dt,
+                        pairs_per_step=pairs, pairs_per_step_note=f"mean over the {args.steps} timed steps, each "
+                        "the count of the plan its force pass ran", particles=n, dt=dt,
                         parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
                         l2="inputs larger than L2 (2.1 GB positions, 3.2 GB FP64 sums)"),
             particles_per_s_per_step=world * n / (t_max * 1e-3),
@@ -383,16 +396,44 @@ def run_forces_only(args):
     return 0
 
 
-def run_batched(args):
-    """Secondary measurement: 64 independent boxes in one persistent launch replayed from a CUDA graph,
-    against one nf_forces launch per box on the same boxes."""
+BATCHED_BOXES = 64
+
+
+def _batched_specs():
+    """The batched workload: 64 independent unit boxes, N log-uniform in [32^3, 128^3] (seeded)."""
+    from synth import generators as gen
+    return gen.batched_boxes(BATCHED_BOXES, gen.rng_for(3))
+
+
+def shard_boxes(n_boxes: int, rank: int, world: int) -> list[int]:
+    """Boxes of one rank: rank, rank + world, rank + 2 world, ...  The boxes are independent, so
+    ranks exchange nothing but the timing and the pair totals."""
+    return list(range(rank, n_boxes, world))
+
+
+def batched_job(pairs_local: int, ms_local: float, world: int) -> tuple[int, float, float]:
+    """Whole-job (pairs, ms, Gpair/s) of a sharded batch: pairs summed over ranks, the slowest rank's time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(pairs_local)], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        pairs = int(round(float(t.item())))
+        ms = max_over_ranks(ms_local)
+    else:
+        pairs, ms = int(pairs_local), float(ms_local)
+    return pairs, ms, pairs / (ms * 1e-3) / 1e9
+
+
+def _time_batched(specs, idx, steps, warmup):
+    """Boxes specs[idx] in one persistent launch replayed from a CUDA graph, against one nf_forces
+    launch per box on the same boxes (CUDA events on the boxes' stream)."""
     import torch
     import paper_1810_02916_b300 as nfb
-    from synth import generators as gen
-    specs = gen.batched_boxes(64, gen.rng_for(3))
     stream = torch.cuda.Stream()
     boxes, outs = [], []
-    for sp in specs:
+    for i in idx:
+        sp = specs[i]
         b = nfb.NearField(sp.cpd, sp.eps)
         b.set_stream(stream)
         b.bin_particles(torch.from_numpy(sp.pos).cuda())
@@ -400,38 +441,68 @@ def run_batched(args):
         outs.append(torch.empty((b.n, 4), dtype=torch.float32, device="cuda"))
     pairs = sum(b.pair_count() for b in boxes)
     n = sum(b.n for b in boxes)
+    out = dict(boxes=len(boxes), particles=n, pairs=pairs, steps=steps)
+    if not boxes:
+        out.update(graph_ms=0.0, per_box_ms=0.0)
+        return out
     with torch.cuda.stream(stream):
         nfb.forces_batched(boxes, outs)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         nfb.forces_batched(boxes, outs)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         g.replay()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     with torch.cuda.stream(stream):
-        for _ in range(args.steps):
+        for _ in range(steps):
             g.replay()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_graph = e0.elapsed_time(e1) / args.steps
+    ms_graph = e0.elapsed_time(e1) / steps
     # one launch per box, same stream
     for b, o in zip(boxes, outs):
         b.forces(o)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for b, o in zip(boxes, outs):
             b.forces(o)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_single = e0.elapsed_time(e1) / args.steps
-    print(json.dumps(dict(mode="batched", boxes=len(boxes), particles=n, pairs=pairs,
-                          batched_graph=dict(ms=ms_graph, gpair_s=pairs / (ms_graph * 1e-3) / 1e9),
-                          one_launch_per_box=dict(ms=ms_single, gpair_s=pairs / (ms_single * 1e-3) / 1e9))),
-          flush=True)
+    ms_single = e0.elapsed_time(e1) / steps
+    for b in boxes:
+        b.close()
+    out.update(graph_ms=ms_graph, graph_gpair_s=pairs / (ms_graph * 1e-3) / 1e9,
+               per_box_ms=ms_single, per_box_gpair_s=pairs / (ms_single * 1e-3) / 1e9,
+               what="one persistent launch over all boxes replayed from a CUDA graph (graph_*) vs one "
+                    "nf_forces launch per box (per_box_*)")
+    return out
+
+
+def run_batched(args):
+    """The batched configuration: 64 independent boxes in one persistent launch replayed from a CUDA
+    graph.  Under torchrun each rank takes its share of the boxes (shard_boxes) on its own GPU; every
+    rank prints its own line and rank 0 the whole job's (pairs summed, slowest rank's time)."""
+    import torch
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")       # only host scalars are reduced
+    torch.cuda.set_device(local)
+    specs = _batched_specs()
+    idx = shard_boxes(len(specs), rank, world)
+    r = _time_batched(specs, idx, args.steps, args.warmup)
+    print(json.dumps(dict(mode="batched", rank=rank, world=world, boxes_of_rank=idx, **r)), flush=True)
+    pairs, ms, gps = batched_job(r["pairs"], r["graph_ms"], world)
+    if rank == 0:
+        print(json.dumps(dict(mode="batched", n_gpus=world, boxes=len(specs), pairs=pairs, ms=ms, gpair_s=gps,
+                              unit=UNIT, scaling="strong", parallelism=f"boxes sharded over {world} rank(s), "
+                              "no data exchange")), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -535,6 +606,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--batched-steps", type=int, default=5,
+                    help="graph replays of the 64-box batch reported beside the bench line (0: skip)")
     ap.add_argument("--cpu-sinks", type=int, default=0, help="0: size the sample to --cpu-seconds")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sinks", type=int, default=0, help="0: size the sample to --ref-seconds")

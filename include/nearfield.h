@@ -50,7 +50,9 @@ enum nf_status {
     NF_EINVAL = 1,   /* bad argument or input data */
     NF_ENOMEM = 2,   /* device or host allocation failed */
     NF_ECUDA = 3,    /* a CUDA call failed (message in nf_last_error) */
-    NF_ETIMEOUT = 4, /* a bounded device-side wait ran out */
+    NF_ETIMEOUT = 4, /* reserved: no call returns it (the kernels of this library
+                        make no device-side waits; the work queue is one atomic
+                        counter) */
     NF_ESTATE = 5    /* call not valid in the box's current state */
 };
 
@@ -141,6 +143,9 @@ double nf_spline_eps_from_plummer(double eps_plummer);
  * multiple of 2^-22 (half to even).  Particles are sorted by cell id, stably
  * in id order.  Velocities are reset to zero.  NF_EINVAL for non-finite
  * positions.  Section 2.1 (cells, cell-centred positions).  Synchronises.
+ * A load that needs larger buffers than the box holds frees the old ones
+ * first: if it then fails (NF_ENOMEM, or NF_EINVAL for the input), the box
+ * is left empty rather than in its previous state.
  */
 int nf_bin_particles(nf_t *nf, const double *xyz, int64_t n);
 
@@ -154,8 +159,9 @@ int nf_bin_particles(nf_t *nf, const double *xyz, int64_t n);
  * Offsets are rounded to multiples of 2^-22 cell widths (half to even).
  * Validated on the device: counts >= 0, sum(counts) = n, cell_offsets is the
  * exclusive scan of counts, offsets finite and within bounds; NF_EINVAL
- * otherwise (state unchanged).  Particle ids are the storage indices.
- * Velocities are reset to zero.  Synchronises.
+ * otherwise (state unchanged, unless the box had to grow: see
+ * nf_bin_particles).  Particle ids are the storage indices.  Velocities are
+ * reset to zero.  Synchronises.
  */
 int nf_set_particles(nf_t *nf, const int64_t *cell_offsets, const int32_t *counts,
                      const float *pos, int64_t n);
@@ -177,9 +183,32 @@ int nf_get_particles(nf_t *nf, int64_t *cell_offsets, int32_t *counts, float *po
 int nf_num_particles(const nf_t *nf, int64_t *n);
 
 /*
+ * nf_generation -- a process-wide counter value that changes whenever the
+ * box's particles change (nf_bin_particles, nf_set_particles, nf_kick_drift,
+ * or a failed load that emptied the box).  A caller that keeps results of an
+ * earlier pass (the autograd wrapper's backward, for one) compares it to tell
+ * whether the box still holds the positions that pass saw.
+ */
+int nf_generation(const nf_t *nf, uint64_t *gen);
+
+/*
+ * nf_fail_allocations -- failure injection for tests of the NF_ENOMEM paths:
+ * after `skip` more successful device allocations made by this library
+ * (process-wide, every box), the next `count` allocations fail with NF_ENOMEM
+ * before cudaMalloc is called.  nf_fail_allocations(0, 0) turns it off.
+ * When a load (nf_bin_particles, nf_set_particles) fails with NF_ENOMEM
+ * after its box had to grow, the box is left empty (no particles; load
+ * again); nf_set_cutoff failing with NF_ENOMEM leaves the box in the exact
+ * mode; nf_create and nf_forces_batched free what they had allocated.
+ */
+int nf_fail_allocations(int64_t skip, int64_t count);
+
+/*
  * nf_pair_count -- number of ordered (sink, source) evaluations one force
  * pass makes: sum over cells of n_c times the particle count of its
- * (2R+1)^3 neighbourhood (self pairs included).  Synchronises.
+ * (2R+1)^3 neighbourhood (self pairs included).  The count is the one the
+ * box's current work plan holds (every load, drift or cut-off change
+ * re-plans); reading it copies 8 bytes to the host.  Synchronises.
  */
 int nf_pair_count(nf_t *nf, int64_t *pairs);
 
@@ -290,8 +319,8 @@ int nf_tune(nf_t *nf, char *report, int report_len);
  * an allocation's implicit synchronisation).  The paper has no counterpart;
  * it is the same pair kernel as nf_forces, driven without a box handle.
  *   cpd, eps, box  as in nf_create (R = 2); 5 <= cpd <= 64
- *   cell_start     device int32[cpd^3 + 1]: first particle of each cell, a
- *                  non-decreasing scan from 0 to n
+ *   cell_start     device int32[cpd^3 + 1] on the current device: first
+ *                  particle of each cell, a non-decreasing scan from 0 to n
  *   pos            device float[4 n], 16-byte aligned: cell-relative offsets
  *                  in cell widths on the 2^-22 grid (as nf_get_particles
  *                  returns them), sorted by cell
@@ -303,12 +332,17 @@ int nf_tune(nf_t *nf, char *report, int report_len);
  * No cudaMalloc, cudaFree or other allocating call is made: the work list
  * and counters live in one fixed device array of 9,439,488 bytes that every GPU
  * loading the library holds until exit.  Its device address is looked up on
- * the first call on each device, so make that first call before any stream
- * capture.  Calls share that array and it keeps the last call's contents:
- * calls whose GPU work overlaps (other streams, other threads) race and must
- * be serialised by the caller.  The call synchronises `stream` once to
- * validate cell_start.  NF_EINVAL for sizes beyond the limits above, host
- * pointers, misaligned arrays or an invalid cell_start; NF_ECUDA otherwise.
+ * the first call on each device (with that device current), so make that
+ * first call before any stream capture.  Calls share that array and it keeps
+ * the last call's contents: calls whose GPU work overlaps (other streams,
+ * other threads) race and must be serialised by the caller.  Every call
+ * validates cell_start on the device and waits for that check on the host (a
+ * device-to-host copy of one flag, then a synchronisation of `stream`) before
+ * it plans and launches the force pass, which it leaves running (async).
+ * pos, acc and cell_start must be device memory of the current device (or
+ * managed memory).  NF_EINVAL for sizes beyond the limits above, host
+ * pointers or another device's pointers, misaligned arrays or an invalid
+ * cell_start; NF_ECUDA otherwise.
  */
 int nf_forces_noalloc(int cpd, double eps, double box, const int32_t *cell_start, const float *pos,
                       int64_t n, float *acc, void *stream, char *err, int err_len);

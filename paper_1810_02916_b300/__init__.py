@@ -29,7 +29,7 @@ EXPORTS = [
     "nf_set_particles", "nf_set_velocities", "nf_get_particles", "nf_num_particles", "nf_pair_count", "nf_forces",
     "nf_get_forces64", "nf_kick_drift", "nf_vjp", "nf_forces_batched", "nf_profile", "nf_profile_read",
     "nf_set_shape", "nf_tune", "nf_forces_noalloc", "nf_set_softening", "nf_spline_eps_from_plummer",
-    "nf_choose_dt", "nf_multipoles", "nf_set_cutoff",
+    "nf_choose_dt", "nf_multipoles", "nf_set_cutoff", "nf_generation", "nf_fail_allocations",
 ]
 
 
@@ -78,6 +78,8 @@ def lib() -> ctypes.CDLL:
             "nf_choose_dt": ([p, d, d, ctypes.POINTER(d), ctypes.POINTER(d)], i),
             "nf_multipoles": ([p, i, p], i),
             "nf_spline_eps_from_plummer": ([d], d),
+            "nf_generation": ([p, ctypes.POINTER(ctypes.c_uint64)], i),
+            "nf_fail_allocations": ([i64, i64], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -156,6 +158,13 @@ class NearField:
     def n(self) -> int:
         v = ctypes.c_int64()
         self._call("nf_num_particles", ctypes.byref(v))
+        return int(v.value)
+
+    @property
+    def generation(self) -> int:
+        """Changes whenever the box's particles change (load, kick-drift)."""
+        v = ctypes.c_uint64()
+        self._call("nf_generation", ctypes.byref(v))
         return int(v.value)
 
     @property
@@ -289,6 +298,13 @@ class NearField:
         buf = ctypes.create_string_buffer(512)
         self._call("nf_tune", buf, 512)
         return buf.value.decode()
+
+
+def fail_allocations(skip: int, count: int) -> None:
+    """Test hook: after `skip` more device allocations, make the next `count` fail (NF_ENOMEM)."""
+    rc = lib().nf_fail_allocations(int(skip), int(count))
+    if rc != NF_OK:
+        raise NearFieldError(rc, "nf_fail_allocations: skip and count must be >= 0")
 
 
 def spline_eps_from_plummer(eps_plummer: float) -> float:

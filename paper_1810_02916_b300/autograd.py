@@ -9,6 +9,9 @@ backward: grad_acc -> grad_pos via nf_vjp (the hand-written adjoint kernel),
 Cell membership is held fixed (the near field is discontinuous when a
 particle changes cell), and the offsets are rounded to the library's 2^-22
 grid in the forward pass; the gradient is that of the unrounded map.
+backward refuses (RuntimeError) when the box's particles changed after the
+forward pass (nf_generation), since the adjoint reads the box's current
+positions.
 """
 from __future__ import annotations
 
@@ -25,11 +28,15 @@ class NearFieldForces(torch.autograd.Function):
         acc = torch.empty_like(pos)
         box.forces(acc)
         ctx.box = box
+        ctx.generation = box.generation
         return acc
 
     @staticmethod
     def backward(ctx, grad_acc):
         box = ctx.box
+        if box.generation != ctx.generation:
+            raise RuntimeError("the box's particles changed between forward and backward (a load or "
+                               "kick-drift ran in between); the adjoint would be that of other positions")
         box.set_stream(torch.cuda.current_stream())
         w = grad_acc.detach().contiguous().clone()
         w[:, 3] = 0

@@ -71,6 +71,7 @@ struct nf_box {
     // cut-off mode (dense far cells through sub-cell moments); cut_nmin = 0: exact
     int64_t cut_nmin = 0, dense_cap = 0;
     int *dslot = nullptr, *dense_cells = nullptr, *n_dense = nullptr;
+    int *nbr_all = nullptr;           // full 125-cell counts (lane-item choice in cut-off mode)
     float *mpole = nullptr;
     const int **nbr_ptr = nullptr;    // device copy of nbr's address (the split planner reads boxes' tables)
     long long wf = 0;                 // resident warps (<= 32 per SM) x balance factor 4
@@ -136,11 +137,30 @@ bool is_device_cached(nf_t *nf, int slot, const void *p)
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Allocation-failure injection for tests (nf_fail_allocations): after
+// g_fail_skip more successful device allocations, the next g_fail_count fail.
+std::mutex g_fail_mu;
+int64_t g_fail_skip = 0, g_fail_count = 0;
+
+bool injected_failure()
+{
+    std::lock_guard<std::mutex> lk(g_fail_mu);
+    if (g_fail_count <= 0) return false;
+    if (g_fail_skip > 0) {
+        --g_fail_skip;
+        return false;
+    }
+    --g_fail_count;
+    return true;
+}
+
 template <class T>
 int dalloc(nf_t *nf, T **p, size_t bytes)
 {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (injected_failure())
+        return fail(nf, NF_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -209,6 +229,12 @@ int ensure_capacity(nf_t *nf, int64_t n)
     if (item_cap + 2 * nf->wf + 64 > INT32_MAX || static_cast<int64_t>(nf::kTile) * (2 * nf->wf + 64) + n > INT32_MAX)
         return fail(nf, NF_EINVAL, "too many particles for one box");
     cudaStreamSynchronize(nf->stream);
+    // the old particles and plan go with their buffers: until a load completes the
+    // box is empty, so no later call can launch on freed or half-built state
+    nf->n = 0;
+    nf->have_particles = false;
+    nf->have_forces = false;
+    nf->generation = ++g_generation;
     free_particles(nf);
     const int64_t c = n < 1 ? 1 : n;
     int rc = NF_OK;
@@ -304,8 +330,13 @@ int ensure_cutoff(nf_t *nf)
 {
     int rc = NF_OK;
     if (!nf->dslot && ((rc = dalloc(nf, &nf->dslot, sizeof(int) * (static_cast<size_t>(nf->ncell) + 1))) ||
-                       (rc = dalloc(nf, &nf->n_dense, sizeof(int) * 4))))
+                       (rc = dalloc(nf, &nf->nbr_all, sizeof(int) * (static_cast<size_t>(nf->ncell) + 2))) ||
+                       (rc = dalloc(nf, &nf->n_dense, sizeof(int) * 4)))) {
+        dfree(nf->dslot);
+        dfree(nf->nbr_all);
+        dfree(nf->n_dense);
         return rc;
+    }
     const int64_t need = nf->n / nf->cut_nmin + 1;
     if (need <= nf->dense_cap) return NF_OK;
     NF_CK(cudaStreamSynchronize(nf->stream));
@@ -324,23 +355,27 @@ int plan(nf_t *nf)
 {
     // neighbourhood sizes and the pass's pair count, the items (occupancy classes, then
     // lane items), then the source split
+    if (nf->cut_nmin > 0) {
+        int rc = ensure_cutoff(nf);
+        if (rc) return rc;
+    }
     NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->cut_nmin, nf->pairs, nf->counts, nf->offsets, nf->nbr,
-                              nf->stream));
+                              nf->nbr_all, nf->stream));
+    // lane cells are chosen on the full neighbourhood: the reduced one of cut-off mode
+    // hides dense far cells, which a lane item would sum pair by pair
+    const int *lane_nbr = nf->cut_nmin > 0 ? nf->nbr_all : nf->nbr;
     NF_CK(nf::zero_device_int(nf->n_raw, nf->stream));
     for (int cls = 0; cls < nf::kClasses; ++cls)
-        NF_CK(nf::plan_items_class(nf->cell_start, nf->nbr, nf->ncell, 0, cls, nf->items_raw, nf->n_raw, nf->counts,
+        NF_CK(nf::plan_items_class(nf->cell_start, lane_nbr, nf->ncell, 0, cls, nf->items_raw, nf->n_raw, nf->counts,
                                    nf->offsets, nf->scan_tmp, nf->stream));
-    NF_CK(nf::plan_lane_items(nf->cell_start, nf->nbr, nf->cpd, 0, nf->items_raw, nf->n_raw, nf->counts,
+    NF_CK(nf::plan_lane_items(nf->cell_start, lane_nbr, nf->cpd, 0, nf->items_raw, nf->n_raw, nf->counts,
                               nf->offsets, nf->scan_tmp, nf->stream));
     NF_CK(nf::split_items(nf->items_raw, nf->n_raw, static_cast<int>(nf->item_cap), nf->nbr_ptr, nf->pairs, nf->wf,
                           kSplitFloor, nf->split_k, nf->split_p, nf->split_r, nf->split_scan, nf->items,
                           nf->n_items, nf->pieces, nf->reduces, nf->n_reduce, nf->stream));
-    if (nf->cut_nmin > 0) {
-        int rc = ensure_cutoff(nf);
-        if (rc) return rc;
+    if (nf->cut_nmin > 0)
         NF_CK(nf::plan_dense_cells(nf->cell_start, nf->ncell, nf->cut_nmin, nf->dslot, nf->dense_cells, nf->n_dense,
                                    nf->counts, nf->offsets, nf->scan_tmp, nf->stream));
-    }
     return NF_OK;
 }
 
@@ -560,7 +595,7 @@ void nf_destroy(nf_t *nf)
     cudaStreamSynchronize(nf->stream);
     free_particles(nf);
     dfree(nf->cell_start); dfree(nf->counts); dfree(nf->offsets); dfree(nf->nbr);
-    dfree(nf->dslot); dfree(nf->dense_cells); dfree(nf->n_dense); dfree(nf->mpole);
+    dfree(nf->dslot); dfree(nf->dense_cells); dfree(nf->n_dense); dfree(nf->mpole); dfree(nf->nbr_all);
     if (nf->scan_tmp) cudaFree(nf->scan_tmp);
     dfree(nf->n_items); dfree(nf->queue); dfree(nf->err); dfree(nf->pairs); dfree(nf->d_box);
     dfree(nf->n_raw); dfree(nf->n_reduce); dfree(nf->nbr_ptr);
@@ -613,7 +648,16 @@ int nf_set_cutoff(nf_t *nf, int64_t n_min)
     nf->cut_nmin = n_min;
     nf->box_dirty = true;
     if (nf->have_particles) {
-        if ((rc = plan(nf))) return rc;
+        if ((rc = plan(nf))) {
+            if (rc == NF_ENOMEM) {
+                // the moment buffers could not be had: back to the exact near field
+                const std::string why = nf->last_error;
+                nf->cut_nmin = 0;
+                if (plan(nf) == NF_OK) cudaStreamSynchronize(nf->stream);
+                nf->last_error = why + " (the box stays in the exact mode)";
+            }
+            return rc;
+        }
         NF_CK(cudaStreamSynchronize(nf->stream));
     }
     return NF_OK;
@@ -761,14 +805,30 @@ int nf_num_particles(const nf_t *nf, int64_t *n)
     return NF_OK;
 }
 
+int nf_generation(const nf_t *nf, uint64_t *gen)
+{
+    if (!nf || !gen) return NF_EINVAL;
+    *gen = nf->generation;
+    return NF_OK;
+}
+
+int nf_fail_allocations(int64_t skip, int64_t count)
+{
+    if (skip < 0 || count < 0) return NF_EINVAL;
+    std::lock_guard<std::mutex> lk(g_fail_mu);
+    g_fail_skip = skip;
+    g_fail_count = count;
+    return NF_OK;
+}
+
 int nf_pair_count(nf_t *nf, int64_t *pairs)
 {
     int rc = check_box(nf);
     if (rc) return rc;
     if (!pairs) return fail(nf, NF_EINVAL, "pairs is NULL");
     if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
-    NF_CK(nf::neighbour_pairs(nf->cell_start, nf->cpd, nf->cut_nmin, nf->pairs, nf->counts, nf->offsets, nf->nbr,
-                              nf->stream));
+    // every change of the particles or of the cut-off re-plans, and the plan keeps its pair
+    // count in nf->pairs, so the count is read, not recomputed
     unsigned long long h = 0;
     NF_CK(cudaMemcpyAsync(&h, nf->pairs, sizeof(h), cudaMemcpyDeviceToHost, nf->stream));
     NF_CK(cudaStreamSynchronize(nf->stream));
@@ -1141,7 +1201,8 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
         std::vector<const unsigned long long *> prs(nbox);
         for (int b = 0; b < nbox; ++b) {
             nf_t *x = boxes[b];
-            NF_CK(nf::neighbour_pairs(x->cell_start, x->cpd, 0, x->pairs, x->counts, x->offsets, x->nbr, nf->stream));
+            NF_CK(nf::neighbour_pairs(x->cell_start, x->cpd, 0, x->pairs, x->counts, x->offsets, x->nbr, nullptr,
+                                      nf->stream));
             nbr[b] = x->nbr;
             prs[b] = x->pairs;
         }

@@ -87,7 +87,9 @@ struct Reduce {
 constexpr int kCutK = 4;
 constexpr int kCutSub = kCutK * kCutK * kCutK;
 constexpr int kCutWords = 10;
-constexpr int kCutMinN = 1024;   // smallest n_min: dense cells never border lane items (<= kLaneMaxT sources)
+// smallest n_min: a dense cell then holds more particles than a lane cell's whole
+// 125-cell neighbourhood may (kLaneMaxT), so no lane item has a dense cell in reach
+constexpr int kCutMinN = 1024;
 
 // Occupancy classes used to order the work queue (largest cells first).
 constexpr int kClasses = 5;
@@ -128,8 +130,8 @@ cudaError_t count_keys(const uint32_t *keys, int n, int *counts, cudaStream_t st
 // ---- planner (nf_plan.cu) ----
 // Items of one box and one occupancy class, appended at items[*n_items]
 // (*n_items is a device int and is advanced).
-// nbr: sources in each cell's neighbourhood (neighbour_pairs), which decides
-// the cells left to lane items.
+// nbr: particles in each cell's full 125-cell neighbourhood (neighbour_pairs;
+// nbr_all in cut-off mode), which decides the cells left to lane items.
 cudaError_t plan_items_class(const int *cell_start, const int *nbr, int ncell, int box_index, int cls, Item *items,
                              int *n_items, int *scratch_counts, int *scratch_offsets, void *scan_temp,
                              cudaStream_t st);
@@ -154,9 +156,12 @@ cudaError_t reduce_partials(const BoxDev *boxes, const Reduce *reduces, const in
 // sources summed directly in each cell's 125-cell neighbourhood into nbr
 // (ncell ints; tmp, tmp2: ncell ints of scratch) and the pass's pair count
 // sum_c n_c nbr_c into *pairs.  With n_min > 0 (cut-off mode) far cells of at
-// least n_min particles are left out (they act through sub-cell moments).
+// least n_min particles are left out (they act through sub-cell moments), and
+// nbr_all (ncell ints) receives the full 125-cell counts, which decide the lane
+// cells (a lane item sums every source pair by pair, so it must not border a
+// dense cell); with n_min = 0 nbr_all is not touched (may be null).
 cudaError_t neighbour_pairs(const int *cell_start, int cpd, int64_t n_min, unsigned long long *pairs, int *tmp,
-                            int *tmp2, int *nbr, cudaStream_t st);
+                            int *tmp2, int *nbr, int *nbr_all, cudaStream_t st);
 // cut-off mode: dslot[c] = rank of cell c among the cells of >= n_min particles
 // (-1 for the others), dense_cells[rank] = c, *n_dense = their number.
 cudaError_t plan_dense_cells(const int *cell_start, int ncell, int64_t n_min, int *dslot, int *dense_cells,

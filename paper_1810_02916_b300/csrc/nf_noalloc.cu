@@ -68,14 +68,17 @@ int say(char *err, int err_len, int code, const char *msg)
     return code;
 }
 
-bool on_device(const void *p)
+// device memory of device `dev` (the kernels run there and make no peer access),
+// or managed memory
+bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -100,12 +103,12 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
         return say(err, err_len, NF_EINVAL, "nf_forces_noalloc: NULL array");
     if ((reinterpret_cast<uintptr_t>(pos) | reinterpret_cast<uintptr_t>(acc)) & 15u)
         return say(err, err_len, NF_EINVAL, "nf_forces_noalloc: pos and acc must be 16-byte aligned");
-    if (!on_device(cell_start) || (n > 0 && (!on_device(pos) || !on_device(acc))))
-        return say(err, err_len, NF_EINVAL, "nf_forces_noalloc: cell_start, pos and acc must be device memory");
-
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return say(err, err_len, NF_ECUDA, "nf_forces_noalloc: no device");
+    if (!on_device(cell_start, dev) || (n > 0 && (!on_device(pos, dev) || !on_device(acc, dev))))
+        return say(err, err_len, NF_EINVAL,
+                   "nf_forces_noalloc: cell_start, pos and acc must be device memory of the current device");
     char *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -153,7 +156,7 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     if (n == 0) return NF_OK;
 
     // work list (items ordered largest cells first), then the descriptor, then the pair kernel
-    NA_CK(nf::neighbour_pairs(cell_start, cpd, 0, pairs, counts, offsets, nbr, st));
+    NA_CK(nf::neighbour_pairs(cell_start, cpd, 0, pairs, counts, offsets, nbr, nullptr, st));
     NA_CK(nf::zero_device_int(n_items, st));
     for (int cls = 0; cls < nf::kClasses; ++cls)
         NA_CK(nf::plan_items_class(cell_start, nbr, ncell, 0, cls, items, n_items, counts, offsets, scan_tmp, st));

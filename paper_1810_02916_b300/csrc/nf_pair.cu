@@ -44,6 +44,7 @@
 // result does not depend on which warp ran which item (bit-reproducible).
 #include <cfloat>
 #include <climits>
+#include <mutex>
 
 #include "nf_internal.cuh"
 
@@ -1024,33 +1025,50 @@ size_t smem_bytes(int warps)
     return static_cast<size_t>(warps) * per_warp_f4<B, COMP, ADJ>() * sizeof(float4);
 }
 
-// Occupancy of one instantiation at `warps` warps per block, computed once
-// (the dynamic shared-memory limit is raised once to the 8-warp size), so a
-// launch makes no attribute or occupancy query and can be stream-captured.
+// Occupancy of one instantiation at `warps` warps per block on the current
+// device, computed once per device (the dynamic shared-memory limit is raised
+// once per device to the 8-warp size), so a later launch makes no attribute or
+// occupancy query and can be stream-captured.  Safe to call from several
+// threads.
+constexpr int kMaxDev = 64;
+std::mutex g_occ_mu;
+
 template <int B, bool COMP, bool ADJ, int SOFT>
 int blocks_per_sm(int warps)
 {
-    static int cache[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
-    static bool attr = false;
+    static int cache[kMaxDev][9];
+    static bool attr[kMaxDev] = {};
+    static bool init = false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    if (!init) {
+        for (int d = 0; d < kMaxDev; ++d)
+            for (int w = 0; w < 9; ++w) cache[d][w] = -1;
+        init = true;
+    }
     auto kern = pair_kernel<B, COMP, ADJ, SOFT>;
-    if (!attr) {
+    if (!attr[dev]) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem_bytes<B, COMP, ADJ>(8))) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
-        attr = true;
+        attr[dev] = true;
     }
-    if (cache[warps] < 0) {
+    if (cache[dev][warps] < 0) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem_bytes<B, COMP, ADJ>(warps)) !=
             cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
-        cache[warps] = per_sm;
+        cache[dev][warps] = per_sm;
     }
-    return cache[warps];
+    return cache[dev][warps];
 }
 
 template <int B, bool COMP, bool ADJ, int SOFT>

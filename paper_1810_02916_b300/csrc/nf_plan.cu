@@ -430,9 +430,17 @@ cudaError_t plan_lane_items(const int *cell_start, const int *nbr, int cpd, int 
 }
 
 cudaError_t neighbour_pairs(const int *cell_start, int cpd, int64_t n_min, unsigned long long *pairs, int *tmp,
-                            int *tmp2, int *nbr, cudaStream_t st)
+                            int *tmp2, int *nbr, int *nbr_all, cudaStream_t st)
 {
     const int ncell = cpd * cpd * cpd;
+    if (n_min > 0) {
+        // cut-off mode: every particle of the 125-cell window, dense cells included (the
+        // lane-item choice must see a dense far cell, which run_lanes would sum pair by pair)
+        occupancy<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, 0, 0, tmp);
+        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr_all, cpd, 2, kR);
+        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(nbr_all, tmp, cpd, 1, kR);
+        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr_all, cpd, 0, kR);
+    }
     // cells summed over the whole 125-cell window (all of them, or those below n_min) ...
     occupancy<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, n_min, 0, tmp);
     window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr, cpd, 2, kR);

@@ -82,3 +82,14 @@ def test_plummer_to_spline_length_is_the_printed_factor(libnf):
     import paper_1810_02916_b300 as nfb
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "spline_law.json")))
     assert nfb.spline_eps_from_plummer(0.01) == pytest.approx(g["eps_s_over_eps_p"] * 0.01, rel=1e-15)
+
+
+def test_failure_hook_validates_its_arguments_without_gpu(libnf):
+    import paper_1810_02916_b300 as nfb
+    L = nfb.lib()
+    assert L.nf_fail_allocations(-1, 1) == nfb.NF_EINVAL
+    assert L.nf_fail_allocations(0, -1) == nfb.NF_EINVAL
+    assert L.nf_fail_allocations(0, 0) == nfb.NF_OK
+    g = ctypes.c_uint64()
+    assert L.nf_generation(None, ctypes.byref(g)) == nfb.NF_EINVAL
+

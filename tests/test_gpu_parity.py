@@ -469,3 +469,91 @@ def test_cutoff_with_lane_items_and_split_pieces():
     dense = np.where(cnt >= n_min, cnt, 0)
     direct = int((cnt * (window(cnt - dense, 2) + window(dense, 1))).sum())
     assert nf.pair_count() == direct
+
+
+def test_cutoff_compact_halo_in_one_particle_per_cell():
+    """A compact halo (one dense cell) in a background of one particle per cell: the
+    background cells at Chebyshev distance 2 from the halo see it only through its sub-cell
+    moments, so none of them may become a lane item (which would sum the halo pair by pair).
+    Every sink in those 98 cells is checked one by one against the cut-off oracle, tightly
+    enough that the exact sum would fail; the direct-pair count matches the window sum."""
+    cpd = 20
+    rng = np.random.default_rng(71)
+    cells = np.arange(cpd ** 3)
+    base = np.stack([cells // (cpd * cpd), (cells // cpd) % cpd, cells % cpd], 1)
+    bg = (base + 0.1 + 0.8 * rng.random(base.shape)) / cpd
+    hc = np.array([10, 9, 11])
+    halo = (hc + 0.5) / cpd + 0.1 / cpd * rng.standard_normal((3000, 3))
+    halo = np.clip(halo, hc / cpd + 1e-6, (hc + 1) / cpd - 1e-6)        # the whole halo in one cell
+    X = np.mod(np.concatenate([bg, halo]), 1.0)
+    eps = 0.02 / cpd
+    n_min = 1024
+    nf = make_box(X, cpd, eps)
+    nf.set_cutoff(n_min)
+    acc = nf.forces()
+    b = oracle_side(X, cpd)
+    hid = (hc[0] * cpd + hc[1]) * cpd + hc[2]
+    assert b.counts[hid] == 3001 and int((b.counts >= n_min).sum()) == 1
+    cxyz = np.stack([np.arange(cpd ** 3) // (cpd * cpd), (np.arange(cpd ** 3) // cpd) % cpd,
+                     np.arange(cpd ** 3) % cpd], 1)
+    dist = np.abs((cxyz - hc + cpd // 2) % cpd - cpd // 2).max(1)
+    ring = np.concatenate([np.arange(b.offsets[c], b.offsets[c + 1]) for c in np.nonzero(dist == 2)[0]])
+    assert ring.size == 98
+    sinks = np.unique(np.concatenate([ring, sample_sinks(b, 4000)]))
+    ref = oracle.cutoff(b, eps, n_min, sinks)
+    exact = oracle.forces(b, eps, sinks=sinks)
+    got = acc[sinks, :3].astype(np.float64)
+    rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    rel_exact = np.linalg.norm(exact - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    on_ring = np.isin(sinks, ring)
+    assert rel_exact[on_ring].max() > 1e-5          # the test can tell the two sums apart
+    assert rel[on_ring].max() <= 2e-6, rel[on_ring].max()
+    s = oracle.error_stats(got, ref)
+    assert s["rms_rel"] <= RMS_TOL, s
+    cnt = b.counts.reshape(cpd, cpd, cpd).astype(np.int64)
+
+    def window(a, r):
+        for ax in range(3):
+            a = sum(np.roll(a, k, axis=ax) for k in range(-r, r + 1))
+        return a
+    dense = np.where(cnt >= n_min, cnt, 0)
+    assert nf.pair_count() == int((cnt * (window(cnt - dense, 2) + window(dense, 1))).sum())
+
+
+# ------------------------------------------------------------------ the paper's largest-cell regime
+
+def _giant_cell_box():
+    """One cell of 200,000 particles (the largest cell late in the paper's run holds over
+    200,000, Section 2.2) and two dense cells at Chebyshev distance 2 from it, in a sparse
+    background (4 particles per cell)."""
+    cpd = 12
+    rng = np.random.default_rng(81)
+    bg = rng.random((4 * cpd ** 3, 3))
+
+    def blob(cell, n, sigma):
+        c = np.asarray(cell, float)
+        x = (c + 0.5) / cpd + sigma / cpd * rng.standard_normal((n, 3))
+        return np.clip(x, c / cpd + 1e-7, (c + 1) / cpd - 1e-7)
+    X = np.concatenate([bg, blob((3, 3, 3), 200000, 0.2), blob((5, 3, 3), 30000, 0.25),
+                        blob((3, 5, 1), 20000, 0.3)])
+    return X, cpd, (1.0 / 100.0) / 40.0
+
+
+def test_giant_cell_splits_across_pieces_and_cells():
+    X, cpd, eps = _giant_cell_box()
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    assert b.counts.max() >= 200000
+    acc1 = nf.forces()
+    acc2 = nf.forces()
+    assert np.array_equal(acc1, acc2)                    # split pieces reduce in a fixed order
+    giant = int(np.argmax(b.counts))
+    rng = np.random.default_rng(82)
+    in_giant = rng.choice(np.arange(b.offsets[giant], b.offsets[giant + 1]), 2000, replace=False)
+    others = rng.choice(b.n, 2000, replace=False)
+    sinks = np.unique(np.concatenate([in_giant, others]))
+    ref, sa, _ = oracle.forces(b, eps, sinks=sinks, with_sumabs=True)
+    s = oracle.error_stats(acc1[sinks, :3], ref, sa)
+    assert s["rms_rel"] <= RMS_TOL and s["max_bound_ratio"] <= BOUND_K, s
+    assert nf.pair_count() == oracle.pair_count(b)
+
