@@ -386,14 +386,45 @@ def run_forces_only(args):
         nf.set_accumulation(nfb.ACC_PLAIN)
     nf.bin_particles(torch.from_numpy(w.pos).cuda())
     acc = torch.empty((nf.n, 4), dtype=torch.float32, device="cuda")
-    nf.profile(True)
+    nf.profile(2 if args.class_profile else True)
     for _ in range(args.forces_only):
         nf.forces(acc)
     k, ms = nf.profile_read()
     pairs = nf.pair_count()
-    print(json.dumps(dict(workload=args.workload, launches=k, ms_per_launch=ms / max(k, 1), pairs=pairs,
-                          gpair_s=pairs / (ms / max(k, 1) * 1e-3) / 1e9)), flush=True)
+    out = dict(workload=args.workload, launches=k, ms_per_launch=ms / max(k, 1), pairs=pairs,
+               gpair_s=pairs / (ms / max(k, 1) * 1e-3) / 1e9)
+    if args.class_profile:
+        peaks, _ = _peaks()
+        out["classes"] = class_table(nf.profile_classes(), pairs * k, k, float(peaks.get("sm_max_mhz", 2032.0)))
+    print(json.dumps(out), flush=True)
     return 0
+
+
+def class_table(raw, pairs_total, launches, sm_mhz, warps_per_sm=24):
+    """Per-item-class breakdown of the pair kernel (profile mode 2).
+
+    busy_share: the class's share of the warps' summed busy cycles.  eff: pairs per warp-cycle
+    against the FMA-lane bound shared by the resident warps (128 lanes / 14 ops per pair per SM
+    cycle over warps_per_sm warps), i.e. how close the class runs to the roofline while it runs.
+    Lane items' pairs are the pass's total minus the tiled items' pairs."""
+    per_warp_bound = FP32_LANES_PER_SM / FMA_OPS_PER_PAIR / warps_per_sm
+    classes = {k: v for k, v in raw.items() if isinstance(v, tuple)}
+    tiled_pairs = sum(v[2] for k, v in classes.items() if not k.startswith("lane"))
+    busy = sum(v[0] for v in classes.values()) or 1
+    rows = {}
+    for name, (cyc, items, pr) in classes.items():
+        if name == "lane items":
+            pr = pairs_total - tiled_pairs
+        if items == 0:
+            continue
+        rows[name] = dict(items=items // launches, pairs=pr // launches, busy_share=cyc / busy,
+                          pair_share=pr / max(pairs_total, 1),
+                          eff=(pr / cyc / per_warp_bound) if cyc else None)
+    life = raw["warp_lifetime_cycles"]
+    return dict(rows=rows, busy_over_lifetime=busy / max(life, 1), warps=raw["warps"] // launches,
+                wall_ms_per_launch=raw["wall_ns"] / 1e6 / launches,
+                lifetime_over_wall=life / max(raw["warps"], 1) / (raw["wall_ns"] * 1e-3 * sm_mhz)
+                if raw["wall_ns"] else None)
 
 
 BATCHED_BOXES = 64
@@ -616,6 +647,8 @@ def main():
     ap.add_argument("--forces-only", type=int, default=0, help="profiling driver: this many force passes")
     ap.add_argument("--cutoff", type=int, default=1024, help="--mode cutoff: n_min of the dense far cells")
     ap.add_argument("--plain", action="store_true", help="profiling driver: plain FP32 accumulation")
+    ap.add_argument("--class-profile", action="store_true",
+                    help="profiling driver: per-item-class clock sums of the pair kernel")
     ap.add_argument("--mode", default="step", choices=["step", "batched", "adjoint", "multipoles", "cutoff"],
                     help="batched / adjoint: secondary measurements (not the bench line)")
     args = ap.parse_args()

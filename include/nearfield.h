@@ -295,10 +295,27 @@ int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc);
  * nf_forces / nf_forces_batched / nf_vjp calls bracket the pair kernel with
  * CUDA events on the box's stream; nf_profile_read returns the number of
  * timed launches and their summed duration in milliseconds (synchronises)
- * and resets both.
+ * and resets both.  enable = 2 also makes the pair kernel sum clock cycles
+ * per class of work item (a diagnostic: the per-item atomics perturb the
+ * timing a little); nf_profile_classes returns and resets those sums.
  */
 int nf_profile(nf_t *nf, int enable);
 int nf_profile_read(nf_t *nf, int64_t *launches, double *ms);
+
+/*
+ * nf_profile_classes -- the per-class sums of enable = 2, NF_PROFILE_WORDS
+ * uint64 words (out must hold at least that many).  Item classes cls =
+ * 2 kind + piece, kind 0: tiles of 65-128 sinks (4 per lane), 1: 33-64 (2 per
+ * lane), 2: 17-32 (1 per lane), 3: <= 16 sinks (sources split over the lanes),
+ * 4: lane items (runs of sparse cells, one sink per lane); piece 1 for a
+ * source piece of a split item.  out[3 cls] = summed warp clock cycles in the
+ * class's items, out[3 cls + 1] = items, out[3 cls + 2] = pairs (0 for lane
+ * items); out[30] = summed warp lifetimes (cycles), out[31] = warps,
+ * out[32] = UINT64_MAX - earliest warp start, out[33] = latest warp exit
+ * (both globaltimer nanoseconds).  Synchronises.
+ */
+#define NF_PROFILE_WORDS 34
+int nf_profile_classes(nf_t *nf, uint64_t *out, int n_out);
 
 /*
  * nf_set_shape / nf_tune -- launch shape of the pair kernel: warps per block

@@ -20,6 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnearfield.so")
 
 NF_OK, NF_EINVAL, NF_ENOMEM, NF_ECUDA, NF_ETIMEOUT, NF_ESTATE = range(6)
+PROFILE_WORDS = 34       # NF_PROFILE_WORDS of include/nearfield.h
 ACC_COMPENSATED, ACC_PLAIN = 0, 1
 SPLINE, PLUMMER = 0, 1
 _STATUS = {1: "NF_EINVAL", 2: "NF_ENOMEM", 3: "NF_ECUDA", 4: "NF_ETIMEOUT", 5: "NF_ESTATE"}
@@ -30,6 +31,7 @@ EXPORTS = [
     "nf_get_forces64", "nf_kick_drift", "nf_vjp", "nf_forces_batched", "nf_profile", "nf_profile_read",
     "nf_set_shape", "nf_tune", "nf_forces_noalloc", "nf_set_softening", "nf_spline_eps_from_plummer",
     "nf_choose_dt", "nf_multipoles", "nf_set_cutoff", "nf_generation", "nf_fail_allocations",
+    "nf_profile_classes",
 ]
 
 
@@ -80,6 +82,7 @@ def lib() -> ctypes.CDLL:
             "nf_spline_eps_from_plummer": ([d], d),
             "nf_generation": ([p, ctypes.POINTER(ctypes.c_uint64)], i),
             "nf_fail_allocations": ([i64, i64], i),
+            "nf_profile_classes": ([p, p, i], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -282,8 +285,27 @@ class NearField:
             pass
 
     # -------------------------------------------------------------- tuning / timing
-    def profile(self, enable: bool = True):
-        self._call("nf_profile", 1 if enable else 0)
+    def profile(self, enable=True):
+        """True / 1: event timing of the pair kernel; 2: also per-item-class clock sums (diagnostic)."""
+        self._call("nf_profile", int(enable) if not isinstance(enable, bool) else (1 if enable else 0))
+
+    PROFILE_KINDS = ("4-sink tiles", "2-sink tiles", "1-sink tiles", "split (<= 16 sinks)", "lane items")
+
+    def profile_classes(self) -> dict:
+        """Per-class sums of profile(2) since the last read: {class name: (cycles, items, pairs)} plus
+        the warps' summed lifetimes and the kernel's wall span (ns)."""
+        out = np.zeros(PROFILE_WORDS, np.uint64)
+        self._call("nf_profile_classes", _ptr(out), PROFILE_WORDS)
+        res = {}
+        for cls in range(10):
+            name = self.PROFILE_KINDS[cls // 2] + (" (piece)" if cls % 2 else "")
+            res[name] = tuple(int(v) for v in out[3 * cls:3 * cls + 3])
+        mx = np.iinfo(np.uint64).max
+        start = int(mx - out[32]) if out[32] else 0
+        res["warp_lifetime_cycles"] = int(out[30])
+        res["warps"] = int(out[31])
+        res["wall_ns"] = int(out[33]) - start if out[33] else 0
+        return res
 
     def profile_read(self):
         """(launches, total ms) of the pair kernel since the last read."""

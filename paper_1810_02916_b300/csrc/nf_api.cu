@@ -19,6 +19,8 @@ using nf::PairShape;
 using nf::Piece;
 using nf::Reduce;
 
+static_assert(nf::kProfWords == NF_PROFILE_WORDS, "the header's profile size is out of date");
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -88,6 +90,8 @@ struct nf_box {
     bool last_dev[4] = {false, false, false, false};
     // profiling
     bool profile = false;
+    bool profile_classes = false;
+    unsigned long long *prof_cls = nullptr;   // nf::kProfWords per-class words of the pair kernel
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
 
@@ -426,8 +430,7 @@ int launch_forces(nf_t *nf, const BoxDev *d_boxes, const Item *items, const int 
         NF_CK(nf::subcell_moments(nf->cell_start, nf->pos, nf->dense_cells, nf->n_dense, nf->dense_cap, nf->mpole,
                                   nf->sm_count, nf->stream));
     NF_CK(nf::launch_pair(d_boxes, items, n_items, queue, nf->acc_mode == NF_ACC_COMPENSATED, adjoint, nf->softening,
-                          nf->shape,
-                          nf->sm_count, nf->stream));
+                          nf->shape, nf->sm_count, nf->stream, nf->profile_classes ? nf->prof_cls : nullptr));
     if (nf->profile) NF_CK(cudaEventRecord(e1, nf->stream));
     return NF_OK;
 }
@@ -600,6 +603,7 @@ void nf_destroy(nf_t *nf)
     dfree(nf->n_items); dfree(nf->queue); dfree(nf->err); dfree(nf->pairs); dfree(nf->d_box);
     dfree(nf->n_raw); dfree(nf->n_reduce); dfree(nf->nbr_ptr);
     if (nf->dt_tmp) cudaFree(nf->dt_tmp);
+    dfree(nf->prof_cls);
     if (nf->stage.p) cudaFree(nf->stage.p);
     for (cudaEvent_t e : nf->ev) cudaEventDestroy(e);
     delete nf;
@@ -982,8 +986,30 @@ int nf_multipoles(nf_t *nf, int order, double *out)
 
 int nf_profile(nf_t *nf, int enable)
 {
-    if (!nf) return NF_EINVAL;
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (enable < 0 || enable > 2) return fail(nf, NF_EINVAL, "enable must be 0, 1 or 2");
+    if (enable == 2 && !nf->prof_cls) {
+        if ((rc = dalloc(nf, &nf->prof_cls, sizeof(unsigned long long) * nf::kProfWords))) return rc;
+        NF_CK(cudaMemsetAsync(nf->prof_cls, 0, sizeof(unsigned long long) * nf::kProfWords, nf->stream));
+    }
     nf->profile = enable != 0;
+    nf->profile_classes = enable == 2;
+    return NF_OK;
+}
+
+int nf_profile_classes(nf_t *nf, uint64_t *out, int n_out)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    if (!out || n_out < nf::kProfWords) return fail(nf, NF_EINVAL, "out needs NF_PROFILE_WORDS words");
+    if (!nf->prof_cls) {
+        std::memset(out, 0, sizeof(uint64_t) * nf::kProfWords);
+        return NF_OK;
+    }
+    NF_CK(cudaMemcpyAsync(out, nf->prof_cls, sizeof(uint64_t) * nf::kProfWords, cudaMemcpyDeviceToHost, nf->stream));
+    NF_CK(cudaMemsetAsync(nf->prof_cls, 0, sizeof(uint64_t) * nf::kProfWords, nf->stream));
+    NF_CK(cudaStreamSynchronize(nf->stream));
     return NF_OK;
 }
 

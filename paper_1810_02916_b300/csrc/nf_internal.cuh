@@ -105,10 +105,25 @@ struct PairShape {
     int blocks;     // persistent grid size (0 = fill the GPU)
 };
 
+// Per-class profile of the pair kernel (a diagnostic; off unless a profile
+// buffer is passed).  Item classes: kind (0: 4-sink tile, 1: 2-sink, 2: 1-sink,
+// 3: <= 16 sinks with the sources split over the lanes, 4: lane item) times
+// (whole neighbourhood, source piece): class = 2 kind + (piece >= 0).  Words
+// (uint64): [3 cls + 0] summed warp clock cycles spent in the class's items,
+// [3 cls + 1] items, [3 cls + 2] pairs (tiled items only; lane items' pairs are
+// the pass's total minus the rest); then [kProfWarp + 0] summed warp lifetimes
+// (cycles, first grab to exit), [+1] warps, [+2] UINT64_MAX - earliest warp
+// start (globaltimer ns), [+3] latest warp exit (globaltimer ns).
+constexpr int kProfClasses = 10;
+constexpr int kProfWarp = 3 * kProfClasses;
+constexpr int kProfWords = kProfWarp + 4;
+
 // ---- pair kernel (nf_pair.cu) ----
 // softening: 0 = compact spline (Section 4.3.1), 1 = Plummer (Eq. eqn:plummer)
+// prof: kProfWords zero-initialised words, or null (no profile)
 cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, int compensated,
-                        int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st);
+                        int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st,
+                        unsigned long long *prof = nullptr);
 int pair_max_blocks_per_sm(int compensated, int adjoint, int softening, PairShape shape);
 
 // ---- scan / sort / binning (nf_sort.cu) ----

@@ -493,9 +493,10 @@ __device__ __forceinline__ void comp_fold_smem(float *c, float &px, float &py, f
     px = py = pz = 0.f;
 }
 
-// S = 0: split mode (<= 16 sinks); S = 1, 2, 4: sinks per lane
+// S = 0: split mode (<= 16 sinks); S = 1, 2, 4: sinks per lane.  Returns the
+// number of sources the item evaluated for each of its sinks.
 template <int S, int B, bool COMP, bool ADJ, int SOFT>
-__device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, float4 *wstage, int *tstart, int *tpre,
+__device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float4 *wstage, int *tstart, int *tpre,
                          float *comp, unsigned char *tslot, int lane)
 {
     constexpr bool SPLIT = (S == 0);
@@ -847,7 +848,7 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
                 o[2] = static_cast<double>(acc[s].hz) + static_cast<double>(acc[s].lz);
             }
         }
-        return;
+        return src_hi - src_lo;
     }
     const double scale = ADJ ? bx.grad_scale : bx.acc_scale;
 #pragma unroll
@@ -867,6 +868,7 @@ __device__ void run_item(const BoxDev &bx, const Item &item, float4 *stage, floa
                     make_float4(static_cast<float>(gx), static_cast<float>(gy), static_cast<float>(gz), 0.f);
         }
     }
+    return src_hi - src_lo;
 }
 
 // A lane item (a run of sparse cells, <= 32 sinks): every lane takes one sink
@@ -981,11 +983,19 @@ __host__ __device__ constexpr int per_warp_f4()
     return (ADJ ? 4 : 2) * B + (COMP ? 192 : 0) + 64 + B / 8;
 }
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 template <int B, bool COMP, bool ADJ, int SOFT>
 __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *__restrict__ boxes,
                                                                   const Item *__restrict__ items,
                                                                   const int *__restrict__ n_items_p,
-                                                                  int *__restrict__ queue)
+                                                                  int *__restrict__ queue,
+                                                                  unsigned long long *__restrict__ prof)
 {
     extern __shared__ __align__(16) float4 smem_f4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -997,6 +1007,12 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
     int *tstart = tabs, *tpre = tabs + 128;
     unsigned char *tslot = reinterpret_cast<unsigned char *>(tabs + 256);
     const int n_items = *n_items_p;
+    long long life0 = 0;
+    unsigned long long wall0 = 0;
+    if (prof) {
+        life0 = clock64();
+        wall0 = global_ns();
+    }
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(queue, 1);
@@ -1005,17 +1021,37 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
         const Item item = items[it];
         const BoxDev &bx = boxes[item_box(item)];
         const int cnt = item_count(item);
-        if (item_is_lanes(item))
+        const long long t0 = prof ? clock64() : 0;
+        int kind, srcs = 0;
+        if (item_is_lanes(item)) {
             run_lanes<COMP, ADJ, SOFT>(bx, item, lane);
-        else if (cnt <= 16)
-            run_item<0, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
-        else if (cnt <= 32)
-            run_item<1, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
-        else if (cnt <= 64)
-            run_item<2, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
-        else
-            run_item<4, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            kind = 4;
+        } else if (cnt <= 16) {
+            srcs = run_item<0, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            kind = 3;
+        } else if (cnt <= 32) {
+            srcs = run_item<1, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            kind = 2;
+        } else if (cnt <= 64) {
+            srcs = run_item<2, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            kind = 1;
+        } else {
+            srcs = run_item<4, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            kind = 0;
+        }
         __syncwarp();
+        if (prof && lane == 0) {
+            const int cls = 2 * kind + (item.piece >= 0 ? 1 : 0);
+            atomicAdd(prof + 3 * cls, static_cast<unsigned long long>(clock64() - t0));
+            atomicAdd(prof + 3 * cls + 1, 1ull);
+            atomicAdd(prof + 3 * cls + 2, static_cast<unsigned long long>(cnt) * static_cast<unsigned long long>(srcs));
+        }
+    }
+    if (prof && lane == 0) {
+        atomicAdd(prof + kProfWarp, static_cast<unsigned long long>(clock64() - life0));
+        atomicAdd(prof + kProfWarp + 1, 1ull);
+        atomicMax(prof + kProfWarp + 2, ~wall0);
+        atomicMax(prof + kProfWarp + 3, global_ns());
     }
 }
 
@@ -1073,13 +1109,13 @@ int blocks_per_sm(int warps)
 
 template <int B, bool COMP, bool ADJ, int SOFT>
 cudaError_t launch_t(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, PairShape shape,
-                     int sm_count, cudaStream_t st)
+                     int sm_count, cudaStream_t st, unsigned long long *prof)
 {
     const int per_sm = blocks_per_sm<B, COMP, ADJ, SOFT>(shape.warps);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int blocks = shape.blocks > 0 ? shape.blocks : sm_count * per_sm;
-    pair_kernel<B, COMP, ADJ, SOFT><<<blocks, shape.warps * 32, smem_bytes<B, COMP, ADJ>(shape.warps), st>>>(boxes, items,
-                                                                                                      n_items, queue);
+    pair_kernel<B, COMP, ADJ, SOFT><<<blocks, shape.warps * 32, smem_bytes<B, COMP, ADJ>(shape.warps), st>>>(
+        boxes, items, n_items, queue, prof);
     return cudaGetLastError();
 }
 
@@ -1112,10 +1148,11 @@ int max_blocks_t(PairShape shape)
     } while (0)
 
 cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, int compensated,
-                        int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st)
+                        int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st,
+                        unsigned long long *prof)
 {
     if (shape.warps < 1 || shape.warps > 8 || (shape.stage != 128 && shape.stage != 256)) return cudaErrorInvalidValue;
-    NF_PAIR_DISPATCH(launch_t, boxes, items, n_items, queue, shape, sm_count, st);
+    NF_PAIR_DISPATCH(launch_t, boxes, items, n_items, queue, shape, sm_count, st, prof);
 }
 
 int pair_max_blocks_per_sm(int compensated, int adjoint, int softening, PairShape shape)

@@ -5,6 +5,10 @@ box was reloaded after its forward pass.
 Failures are made on the host (nf_fail_allocations fails an allocation before
 cudaMalloc is called); nothing here faults the GPU.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -13,6 +17,7 @@ from synth import generators as gen
 from tests.gpu_helpers import BOUND_K, RMS_TOL, make_box, oracle_side, require_cuda, sample_sinks
 
 pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(autouse=True)
@@ -93,23 +98,37 @@ def test_cutoff_that_cannot_allocate_stays_exact():
     assert s["rms_rel"] <= RMS_TOL, s
 
 
-@pytest.mark.parametrize("skip", [0, 5])
-def test_batched_launch_that_cannot_allocate_recovers(skip):
+def _batched_enomem_in_fresh_process(skip):
+    """Run inside a fresh process, where no batch plan exists yet: the first batched call must
+    allocate its plan (17 device buffers), and the skip-th allocation of it fails."""
+    import torch
     import paper_1810_02916_b300 as nfb
     rng = np.random.default_rng(4)
     specs = gen.batched_boxes(3, rng, n_lo=2000, n_hi=8000)
     boxes = [make_box(s.pos, s.cpd, s.eps) for s in specs]
+    outs = [torch.zeros((b.n, 4), device="cuda") for b in boxes]     # device outputs: no staging buffers
     nfb.fail_allocations(skip, 1)
-    with pytest.raises(nfb.NearFieldError) as e:
-        nfb.forces_batched(boxes)
-    assert e.value.code == nfb.NF_ENOMEM
+    try:
+        nfb.forces_batched(boxes, outs)
+        raise AssertionError("the batched call did not fail")
+    except nfb.NearFieldError as e:
+        assert e.code == nfb.NF_ENOMEM, e
     nfb.fail_allocations(0, 0)
-    outs = nfb.forces_batched(boxes)
+    nfb.forces_batched(boxes, outs)
     for s, acc in zip(specs, outs):
         b = oracle_side(s.pos, s.cpd)
         ref, sa, _ = oracle.forces(b, s.eps, with_sumabs=True)
-        st = oracle.error_stats(acc[:, :3], ref, sa)
+        st = oracle.error_stats(acc.cpu().numpy()[:, :3], ref, sa)
         assert st["rms_rel"] <= RMS_TOL and st["max_bound_ratio"] <= BOUND_K, st
+    print("batched enomem ok")
+
+
+@pytest.mark.parametrize("skip", [0, 5, 16])
+def test_batched_launch_that_cannot_allocate_recovers(skip):
+    code = f"import tests.test_gpu_failures as t; t._batched_enomem_in_fresh_process({skip})"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
+    assert "batched enomem ok" in r.stdout
 
 
 def test_backward_refuses_a_box_reloaded_after_forward():
