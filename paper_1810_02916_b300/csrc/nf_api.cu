@@ -43,7 +43,7 @@ struct nf_box {
     int softening = NF_SPLINE;
     PairShape shape{8, 128, 0};
 
-    int64_t n = 0, cap = 0, item_cap = 0;
+    int64_t n = 0, cap = 0, item_cap = 0, split_cap = 0;   // split_cap: items after source splitting
     bool have_particles = false, have_forces = false;
     uint64_t generation = 0;
 
@@ -248,17 +248,18 @@ int ensure_capacity(nf_t *nf, int64_t n)
         (rc = dalloc(nf, &nf->acc64, 3 * sizeof(double) * static_cast<size_t>(c))) ||
         (rc = dalloc(nf, &nf->keys[0], u4)) || (rc = dalloc(nf, &nf->keys[1], u4)) ||
         (rc = dalloc(nf, &nf->vals[0], u4)) || (rc = dalloc(nf, &nf->vals[1], u4)) ||
-        (rc = dalloc(nf, &nf->xq_by_id, f4)) || (rc = dalloc(nf, &nf->vel_by_id, f4)) ||
-        (rc = dalloc(nf, &nf->items_raw, sizeof(Item) * static_cast<size_t>(item_cap)))) {
+        (rc = dalloc(nf, &nf->xq_by_id, f4)) || (rc = dalloc(nf, &nf->vel_by_id, f4))) {
         free_particles(nf);
         return rc;
     }
-    // splitting adds fewer than 2 wf items and reduce records, and at most 128 (2 wf) + n partial slots
+    // splitting adds fewer than 2 wf items and reduce records, and at most 128 (2 wf) + n partial slots;
+    // items_raw holds the split list's partition too, so both lists have the split capacity
     const int64_t extra = 2 * nf->wf + 64;
     const size_t split_items_cap = static_cast<size_t>(item_cap + extra);
     const size_t slots = static_cast<size_t>(nf::kTile * extra + c);
-    const size_t scan_ints = static_cast<size_t>(item_cap) + 1;
-    if ((rc = dalloc(nf, &nf->items, sizeof(Item) * split_items_cap)) ||
+    const size_t scan_ints = split_items_cap + 1;
+    if ((rc = dalloc(nf, &nf->items_raw, sizeof(Item) * split_items_cap)) ||
+        (rc = dalloc(nf, &nf->items, sizeof(Item) * split_items_cap)) ||
         (rc = dalloc(nf, &nf->pieces, sizeof(Piece) * split_items_cap)) ||
         (rc = dalloc(nf, &nf->reduces, sizeof(Reduce) * static_cast<size_t>(extra))) ||
         (rc = dalloc(nf, &nf->partials, 3 * sizeof(double) * slots)) ||
@@ -277,6 +278,7 @@ int ensure_capacity(nf_t *nf, int64_t n)
     }
     nf->cap = c;
     nf->item_cap = item_cap;
+    nf->split_cap = static_cast<int64_t>(split_items_cap);
     nf->box_dirty = true;
     return NF_OK;
 }
@@ -377,6 +379,10 @@ int plan(nf_t *nf)
     NF_CK(nf::split_items(nf->items_raw, nf->n_raw, static_cast<int>(nf->item_cap), nf->nbr_ptr, nf->pairs, nf->wf,
                           kSplitFloor, nf->split_k, nf->split_p, nf->split_r, nf->split_scan, nf->items,
                           nf->n_items, nf->pieces, nf->reduces, nf->n_reduce, nf->stream));
+    // heavy items first, light ones after (the pair kernel's two queues)
+    NF_CK(nf::partition_light(nf->items, nf->n_items, static_cast<int>(nf->split_cap), nf->split_k, nf->split_scan,
+                              nf->items_raw, nf->stream));
+    std::swap(nf->items, nf->items_raw);
     if (nf->cut_nmin > 0)
         NF_CK(nf::plan_dense_cells(nf->cell_start, nf->ncell, nf->cut_nmin, nf->dslot, nf->dense_cells, nf->n_dense,
                                    nf->counts, nf->offsets, nf->scan_tmp, nf->stream));
@@ -412,7 +418,7 @@ int read_err(nf_t *nf, int *host)
 
 int launch_forces(nf_t *nf, const BoxDev *d_boxes, const Item *items, const int *n_items, int *queue, int adjoint)
 {
-    NF_CK(cudaMemsetAsync(queue, 0, sizeof(int), nf->stream));
+    NF_CK(cudaMemsetAsync(queue, 0, 2 * sizeof(int), nf->stream));   // heavy and light queue
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (nf->profile) {
         while (nf->ev.size() < nf->ev_used + 2) {
@@ -1128,7 +1134,7 @@ struct Batch {
     const int **nbr_ptrs = nullptr;
     const unsigned long long **pair_ptrs = nullptr;
     unsigned long long *total = nullptr;
-    int64_t raw_cap = 0, n_cap = 0;
+    int64_t raw_cap = 0, n_cap = 0, split_cap = 0;
     int nbox_cap = 0, reduce_cap = 0;
     int *n_raw = nullptr, *n_items = nullptr, *n_reduce = nullptr, *queue = nullptr;
     int device = -1;
@@ -1166,11 +1172,11 @@ int batch_alloc(nf_t *nf, Batch &B, int nbox, int64_t raw_cap, int64_t n_total)
     batch_release(B);
     const int64_t extra = 2 * nf->wf + 64;
     const size_t items_cap = static_cast<size_t>(raw_cap + extra);
-    const size_t scan_ints = static_cast<size_t>(raw_cap) + 1;
+    const size_t scan_ints = items_cap + 1;
     const size_t slots = static_cast<size_t>(nf::kTile * extra + n_total);
     int rc;
     if ((rc = dalloc(nf, &B.d_desc, sizeof(BoxDev) * nbox)) ||
-        (rc = dalloc(nf, &B.items_raw, sizeof(Item) * static_cast<size_t>(raw_cap))) ||
+        (rc = dalloc(nf, &B.items_raw, sizeof(Item) * items_cap)) ||
         (rc = dalloc(nf, &B.items, sizeof(Item) * items_cap)) || (rc = dalloc(nf, &B.pieces, sizeof(Piece) * items_cap)) ||
         (rc = dalloc(nf, &B.reduces, sizeof(Reduce) * static_cast<size_t>(extra))) ||
         (rc = dalloc(nf, &B.partials, 3 * sizeof(double) * slots)) ||
@@ -1186,6 +1192,7 @@ int batch_alloc(nf_t *nf, Batch &B, int nbox, int64_t raw_cap, int64_t n_total)
         return rc;
     }
     B.raw_cap = raw_cap;
+    B.split_cap = static_cast<int64_t>(items_cap);
     B.n_cap = n_total;
     B.nbox_cap = nbox;
     B.reduce_cap = static_cast<int>(extra);
@@ -1247,6 +1254,9 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
         NF_CK(nf::split_items(B.items_raw, B.n_raw, static_cast<int>(B.raw_cap), B.nbr_ptrs, B.total, nf->wf,
                               kSplitFloor, B.split_k, B.split_p, B.split_r, B.split_scan, B.items, B.n_items, B.pieces,
                               B.reduces, B.n_reduce, nf->stream));
+        NF_CK(nf::partition_light(B.items, B.n_items, static_cast<int>(B.split_cap), B.split_k, B.split_scan,
+                                  B.items_raw, nf->stream));
+        std::swap(B.items, B.items_raw);
         NF_CK(cudaStreamSynchronize(nf->stream));   // the host vectors above must outlive their copies
         B.boxes.assign(boxes, boxes + nbox);
         B.gens.resize(nbox);

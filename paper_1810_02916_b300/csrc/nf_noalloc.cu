@@ -40,8 +40,8 @@ constexpr size_t kOffCounts = align256(kOffItems + sizeof(nf::Item) * static_cas
 constexpr size_t kOffOffsets = align256(kOffCounts + sizeof(int) * kCellInts);
 constexpr size_t kOffNbr = align256(kOffOffsets + sizeof(int) * kCellInts);
 constexpr size_t kOffScan = align256(kOffNbr + sizeof(int) * kCellInts);
-constexpr size_t kOffWords = align256(kOffScan + sizeof(int) * kScanInts);   // n_items, queue, error flag
-constexpr size_t kOffPairs = align256(kOffWords + 4 * sizeof(int));          // the pass's pair count
+constexpr size_t kOffWords = align256(kOffScan + sizeof(int) * kScanInts);   // item counts, queues, error flag
+constexpr size_t kOffPairs = align256(kOffWords + 8 * sizeof(int));          // the pass's pair count
 constexpr size_t kScratchBytes = align256(kOffPairs + sizeof(unsigned long long));
 
 static_assert(kScratchBytes == 9439488, "the documented scratch size is out of date");
@@ -131,7 +131,7 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     int *nbr = reinterpret_cast<int *>(base + kOffNbr);
     void *scan_tmp = base + kOffScan;
     int *words = reinterpret_cast<int *>(base + kOffWords);
-    int *n_items = words, *queue = words + 1, *bad = words + 2;
+    int *n_items = words, *queue = words + 2, *bad = words + 4;   // n_items[2], queue[2]
     unsigned long long *pairs = reinterpret_cast<unsigned long long *>(base + kOffPairs);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int ncell = cpd * cpd * cpd;
@@ -161,6 +161,7 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     for (int cls = 0; cls < nf::kClasses; ++cls)
         NA_CK(nf::plan_items_class(cell_start, nbr, ncell, 0, cls, items, n_items, counts, offsets, scan_tmp, st));
     NA_CK(nf::plan_lane_items(cell_start, nbr, cpd, 0, items, n_items, counts, offsets, scan_tmp, st));
+    NA_CK(nf::all_items_heavy(n_items, st));   // one list in plan order, no light queue
     const double inv_w = static_cast<double>(cpd) / box;
     const double ec = eps * inv_w;
     nf::BoxDev d{};
@@ -179,7 +180,7 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     d.grad_scale = inv_w * inv_w * inv_w;
     write_desc<<<1, 1, 0, st>>>(desc, d);
     NA_CK(cudaGetLastError());
-    NA_CK(cudaMemsetAsync(queue, 0, sizeof(int), st));
+    NA_CK(cudaMemsetAsync(queue, 0, 2 * sizeof(int), st));
     int sms = 0;
     NA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     NA_CK(nf::launch_pair(desc, items, n_items, queue, 1, 0, 0, nf::PairShape{8, 128, 0}, sms, st));

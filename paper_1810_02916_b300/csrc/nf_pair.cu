@@ -75,6 +75,9 @@ namespace {
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
+#ifndef NF_LIGHT_WARPS
+#define NF_LIGHT_WARPS 2   // of every 8 warps of a block, this many start on the light queue
+#endif
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kFar = 1.0e18f;   // padding source: y^3 underflows to 0, contributes exactly zero
@@ -1006,7 +1009,11 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
     int *tabs = reinterpret_cast<int *>(w0 + (ADJ ? 4 : 2) * B + (COMP ? 192 : 0));
     int *tstart = tabs, *tpre = tabs + 128;
     unsigned char *tslot = reinterpret_cast<unsigned char *>(tabs + 256);
-    const int n_items = *n_items_p;
+    const int n_items = n_items_p[0];
+    const int n_heavy = min(n_items_p[1], n_items);
+    // two queues: heavy items [0, n_heavy) and light items [n_heavy, n_items); a warp
+    // starts on one and moves to the other once it is empty
+    int q = (warp < NF_LIGHT_WARPS * static_cast<int>(blockDim.x >> 5) / 8) ? 1 : 0;
     long long life0 = 0;
     unsigned long long wall0 = 0;
     if (prof) {
@@ -1014,10 +1021,21 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
         wall0 = global_ns();
     }
     for (;;) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(queue, 1);
+        int it = -1;
+        if (lane == 0) {
+            for (int k = 0; k < 2 && it < 0; ++k) {
+                if (q == 0) {
+                    const int t = atomicAdd(queue, 1);
+                    if (t < n_heavy) it = t;
+                } else {
+                    const int t = n_heavy + atomicAdd(queue + 1, 1);
+                    if (t < n_items) it = t;
+                }
+                if (it < 0) q ^= 1;
+            }
+        }
         it = __shfl_sync(kFull, it, 0);
-        if (it >= n_items) break;
+        if (it < 0) break;
         const Item item = items[it];
         const BoxDev &bx = boxes[item_box(item)];
         const int cnt = item_count(item);

@@ -333,7 +333,48 @@ __global__ void reduce_kernel(const BoxDev *__restrict__ boxes, const Reduce *__
         bx.acc_out[idx] = make_float4(static_cast<float>(gx), static_cast<float>(gy), static_cast<float>(gz), 0.f);
 }
 
+// flags[i] = 1 for a heavy item at i < n, 0 elsewhere (i <= cap)
+__global__ void heavy_flags(const Item *__restrict__ items, const int *__restrict__ n_p, int cap, int *__restrict__ flags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > cap) return;
+    flags[i] = (i < *n_p && !item_is_light(items[i])) ? 1 : 0;
+}
+
+// flags hold the exclusive scan of the heavy flags here
+__global__ void partition_scatter(const Item *__restrict__ items, int *__restrict__ n_items,
+                                  const int *__restrict__ pos, Item *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = n_items[0];
+    const int n_heavy = pos[n];
+    if (i == 0) n_items[1] = n_heavy;
+    if (i >= n) return;
+    const Item it = items[i];
+    const int h = pos[i];
+    out[item_is_light(it) ? n_heavy + (i - h) : h] = it;
+}
+
+__global__ void copy_count(int *n_items) { n_items[1] = n_items[0]; }
+
 }  // namespace
+
+cudaError_t partition_light(const Item *items_in, int *n_items, int cap, int *flags, void *scan_temp,
+                            Item *items_out, cudaStream_t st)
+{
+    const int64_t m = static_cast<int64_t>(cap) + 1;
+    heavy_flags<<<nblocks(m, 256), 256, 0, st>>>(items_in, n_items, cap, flags);
+    cudaError_t e = exclusive_scan_i32(flags, flags, m, scan_temp, st);
+    if (e != cudaSuccess) return e;
+    partition_scatter<<<nblocks(m, 256), 256, 0, st>>>(items_in, n_items, flags, items_out);
+    return cudaGetLastError();
+}
+
+cudaError_t all_items_heavy(int *n_items, cudaStream_t st)
+{
+    copy_count<<<1, 1, 0, st>>>(n_items);
+    return cudaGetLastError();
+}
 
 __global__ void sum_kernel(const unsigned long long *const *ptrs, int n, unsigned long long *out)
 {

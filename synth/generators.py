@@ -300,14 +300,26 @@ def _clustered64():
     return _clustered(64, cpd=25, config=5)
 
 
+def _tiles128(cpd: int = 40, per_cell: int = 128):
+    """Exactly per_cell particles in every cell, uniform within it (cpd^3 cells): every work
+    item is one full 128-sink tile against 125 x 128 sources (a profiling workload)."""
+    rng = rng_for(6)
+    c = np.repeat(np.arange(cpd ** 3), per_cell)
+    base = np.stack([c // (cpd * cpd), (c // cpd) % cpd, c % cpd], 1)
+    pos = (base + rng.random(base.shape)) / cpd
+    n = pos.shape[0]
+    return Workload(f"tiles{per_cell}", pos, cpd, (1.0 / n ** (1.0 / 3.0)) / 40.0, meta=dict(per_cell=per_cell))
+
+
 WORKLOADS = {
     "uniform32k": _uniform32k,
     "clustered256": _clustered,
     "zeldovich512": _zeldovich,
     "clustered64": _clustered64,
+    "tiles128": _tiles128,
 }
 
 
 def workload(name: str, **kw) -> Workload:
-    """Named workload: uniform32k, clustered256, zeldovich512, clustered64."""
+    """Named workload: uniform32k, clustered256, zeldovich512, clustered64, tiles128."""
     return WORKLOADS[name](**kw)
