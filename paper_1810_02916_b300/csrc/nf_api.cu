@@ -379,7 +379,7 @@ int plan(nf_t *nf)
     NF_CK(nf::split_items(nf->items_raw, nf->n_raw, static_cast<int>(nf->item_cap), nf->nbr_ptr, nf->pairs, nf->wf,
                           kSplitFloor, nf->split_k, nf->split_p, nf->split_r, nf->split_scan, nf->items,
                           nf->n_items, nf->pieces, nf->reduces, nf->n_reduce, nf->stream));
-    // heavy items first, light ones after (the pair kernel's two queues)
+    // heavy items first, light ones after
     NF_CK(nf::partition_light(nf->items, nf->n_items, static_cast<int>(nf->split_cap), nf->split_k, nf->split_scan,
                               nf->items_raw, nf->stream));
     std::swap(nf->items, nf->items_raw);
@@ -418,7 +418,7 @@ int read_err(nf_t *nf, int *host)
 
 int launch_forces(nf_t *nf, const BoxDev *d_boxes, const Item *items, const int *n_items, int *queue, int adjoint)
 {
-    NF_CK(cudaMemsetAsync(queue, 0, 2 * sizeof(int), nf->stream));   // heavy and light queue
+    NF_CK(cudaMemsetAsync(queue, 0, sizeof(int), nf->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (nf->profile) {
         while (nf->ev.size() < nf->ev_used + 2) {

@@ -73,10 +73,8 @@ constexpr int kLaneMaxCells = 32;
 __host__ __device__ inline bool lane_cell(int n, int nbr) { return n == 0 || (n <= kLaneMaxN && nbr <= kLaneMaxT); }
 
 // Light items: lane items and tiles of at most 16 sinks (the sources split over
-// the lanes).  They spend much of their time waiting on memory (the neighbour
-// table, the first staged round), so the plan lists them after every heavy item
-// and the pair kernel lets a few warps of each block start on them (a second
-// queue), which keeps their latency under the heavy items' FP32 work.
+// the lanes).  The plan lists them after every heavy item, so the queue runs all
+// tiles of more than 16 sinks (largest cells first) before any light item.
 __host__ __device__ inline bool item_is_light(const Item &it) { return item_is_lanes(it) || item_count(it) <= 16; }
 
 // Sinks of a split item whose partials are summed (in piece order) by reduce_partials.
@@ -127,8 +125,6 @@ constexpr int kProfWords = kProfWarp + 4;
 
 // ---- pair kernel (nf_pair.cu) ----
 // softening: 0 = compact spline (Section 4.3.1), 1 = Plummer (Eq. eqn:plummer)
-// n_items[0]: items, n_items[1]: heavy items (listed first; see item_is_light);
-// queue: two zeroed counters (heavy, light)
 // prof: kProfWords zero-initialised words, or null (no profile)
 cudaError_t launch_pair(const BoxDev *boxes, const Item *items, const int *n_items, int *queue, int compensated,
                         int adjoint, int softening, PairShape shape, int sm_count, cudaStream_t st,
@@ -173,14 +169,11 @@ cudaError_t split_items(const Item *items_in, const int *n_in, int item_cap, con
                         const unsigned long long *total_pairs, long long warps_x_f, int t_floor, int *k, int *p,
                         int *r, void *scan_temp, Item *items_out, int *n_out, Piece *pieces, Reduce *reduces,
                         int *n_reduce, cudaStream_t st);
-// Stable partition of items_in[0, n_in[0]) into items_out: heavy items first,
-// then light ones; n_items[1] = number of heavy items (n_items[0] is the total
-// and is not changed; n_items may be n_in).  flags: cap + 1 ints of scratch,
-// scan_temp: scan_temp_bytes(cap + 1).
+// Stable partition of items_in[0, n_items[0]) into items_out: heavy items first,
+// then light ones (n_items[1] receives the number of heavy items).  flags:
+// cap + 1 ints of scratch, scan_temp: scan_temp_bytes(cap + 1).
 cudaError_t partition_light(const Item *items_in, int *n_items, int cap, int *flags, void *scan_temp,
                             Item *items_out, cudaStream_t st);
-// n_items[1] = n_items[0]: every item in the first queue (a list not partitioned)
-cudaError_t all_items_heavy(int *n_items, cudaStream_t st);
 // *out = sum of the n values at ptrs[0..n)
 cudaError_t sum_pair_counts(const unsigned long long *const *ptrs, int n, unsigned long long *out, cudaStream_t st);
 cudaError_t reduce_partials(const BoxDev *boxes, const Reduce *reduces, const int *n_reduce, int max_reduce,

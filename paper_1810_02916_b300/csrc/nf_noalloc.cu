@@ -161,7 +161,6 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     for (int cls = 0; cls < nf::kClasses; ++cls)
         NA_CK(nf::plan_items_class(cell_start, nbr, ncell, 0, cls, items, n_items, counts, offsets, scan_tmp, st));
     NA_CK(nf::plan_lane_items(cell_start, nbr, cpd, 0, items, n_items, counts, offsets, scan_tmp, st));
-    NA_CK(nf::all_items_heavy(n_items, st));   // one list in plan order, no light queue
     const double inv_w = static_cast<double>(cpd) / box;
     const double ec = eps * inv_w;
     nf::BoxDev d{};
@@ -180,7 +179,7 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     d.grad_scale = inv_w * inv_w * inv_w;
     write_desc<<<1, 1, 0, st>>>(desc, d);
     NA_CK(cudaGetLastError());
-    NA_CK(cudaMemsetAsync(queue, 0, 2 * sizeof(int), st));
+    NA_CK(cudaMemsetAsync(queue, 0, sizeof(int), st));
     int sms = 0;
     NA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     NA_CK(nf::launch_pair(desc, items, n_items, queue, 1, 0, 0, nf::PairShape{8, 128, 0}, sms, st));

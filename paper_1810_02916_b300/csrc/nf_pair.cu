@@ -75,8 +75,11 @@ namespace {
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
-#ifndef NF_LIGHT_WARPS
-#define NF_LIGHT_WARPS 2   // of every 8 warps of a block, this many start on the light queue
+#ifndef NF_PAIR_UNROLL
+#define NF_PAIR_UNROLL 2   // source pairs per unrolled step on lanes holding one sink
+#endif
+#ifndef NF_UNROLL_S2
+#define NF_UNROLL_S2 NF_SRC_UNROLL   // staged sources per unrolled step on lanes holding two sinks
 #endif
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -569,6 +572,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
     // the softening-length bound, so a self pair's r^2 = FLT_MIN is always below it.
     constexpr bool VOTE = NF_NEAR_VOTE && FARSPLIT && !ADJ && SS >= 2;
     constexpr bool VOTE1 = NF_NEAR_VOTE && FARSPLIT && PAIRSRC && !SPLIT;   // one sink, source pairs
+    constexpr bool VOTE_SPLIT = NF_NEAR_VOTE && FARSPLIT && PAIRSRC && SPLIT;   // <= 16 sinks, source pairs
     // the whole flattened neighbourhood, or this item's piece of it
     int src_lo = 0, src_hi = total;
     if (item.piece >= 0) {
@@ -598,18 +602,48 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         const float2 *xs2 = reinterpret_cast<const float2 *>(buf);   // PAIRSRC layout: x, y, z arrays
         const float2 *ys2 = xs2 + B / 2, *zs2 = xs2 + B;
         if (SPLIT && PAIRSRC) {
-            // source pair m = entries 2m, 2m + 1; the pair holding the last near entry
-            // takes the full law (exact for its far partner); entries >= nr are padding
+            // Lane group g takes the source pairs g, g + splits, ... (pair m = entries 2m, 2m + 1),
+            // two pairs per step.  Every lane runs the same number of steps: pairs past the round's
+            // last entry are padding (exact zeros), and a round holds B/2 pairs, a multiple of
+            // 2 splits, so the steps stay inside the buffer.  The warp therefore stays converged and
+            // votes as the tiled paths do: a near step takes the spline tail only when some lane
+            // finds a pair within eps.  The pair holding the last near entry counts as near (the
+            // full law is exact for its far partner).
             const int nnp = (nn + 1) >> 1, nrp = (nr + 1) >> 1;
-            int m = my_split;
-            for (; m < nnp; m += splits)
-                pair_force2<SOFT>(xs2[m], ys2[m], zs2[m], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0], a02, a12,
-                                  a22, e22);
+            const int n_near = ((nnp + splits - 1) / splits + 1) & ~1;
+            const int n_all = ((nrp + splits - 1) / splits + 1) & ~1;
+            for (int i = 0; i < n_near; i += 2) {
+                const int m0 = my_split + i * splits, m1 = m0 + splits;
+                if (VOTE_SPLIT) {
+                    const float2 dx0 = __fadd2_rn(xs2[m0], nx2[0]), dy0 = __fadd2_rn(ys2[m0], ny2[0]),
+                                 dz0 = __fadd2_rn(zs2[m0], nz2[0]);
+                    const float2 dx1 = __fadd2_rn(xs2[m1], nx2[0]), dy1 = __fadd2_rn(ys2[m1], ny2[0]),
+                                 dz1 = __fadd2_rn(zs2[m1], nz2[0]);
+                    const float2 fm = make_float2(FLT_MIN, FLT_MIN);
+                    const float2 r20 = __ffma2_rn(dz0, dz0, __ffma2_rn(dy0, dy0, __ffma2_rn(dx0, dx0, fm)));
+                    const float2 r21 = __ffma2_rn(dz1, dz1, __ffma2_rn(dy1, dy1, __ffma2_rn(dx1, dx1, fm)));
+                    if (__any_sync(kFull, fminf(fminf(r20.x, r20.y), fminf(r21.x, r21.y)) < eps2)) {
+                        tail2_spline(dx0, dy0, dz0, r20, ax2[0], ay2[0], az2[0], a02, a12, a22);
+                        tail2_spline(dx1, dy1, dz1, r21, ax2[0], ay2[0], az2[0], a02, a12, a22);
+                    } else {
+                        tail2_newton(dx0, dy0, dz0, r20, ax2[0], ay2[0], az2[0]);
+                        tail2_newton(dx1, dy1, dz1, r21, ax2[0], ay2[0], az2[0]);
+                    }
+                } else {
+                    pair_force2<SOFT>(xs2[m0], ys2[m0], zs2[m0], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0],
+                                      a02, a12, a22, e22);
+                    pair_force2<SOFT>(xs2[m1], ys2[m1], zs2[m1], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0],
+                                      a02, a12, a22, e22);
+                }
+            }
             if (FARSPLIT)
-                for (; m < nrp; m += splits)
-                    pair_force2_far(xs2[m], ys2[m], zs2[m], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0]);
+                for (int i = n_near; i < n_all; i += 2) {
+                    const int m0 = my_split + i * splits, m1 = m0 + splits;
+                    pair_force2_far(xs2[m0], ys2[m0], zs2[m0], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0]);
+                    pair_force2_far(xs2[m1], ys2[m1], zs2[m1], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0]);
+                }
         } else if (PAIRSRC) {
-            constexpr int U2 = NF_SRC_UNROLL / 2;
+            constexpr int U2 = NF_PAIR_UNROLL;
             const int nrp = (nr + 2 * U2 - 1) / (2 * U2) * U2;   // padding pairs add exact zeros
             const int nnp = FARSPLIT ? (nn + 2 * U2 - 1) / (2 * U2) * U2 : nrp;
             for (int m = 0; m < nnp; m += U2) {
@@ -650,7 +684,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
             if (FARSPLIT && !ADJ)
                 for (; j < nr; j += splits) pair_force_far(buf[j], xi[0], yi[0], zi[0], px[0], py[0], pz[0]);
         } else {
-            constexpr int U = NF_SRC_UNROLL;
+            constexpr int U = SS == 2 ? NF_UNROLL_S2 : NF_SRC_UNROLL;
             // padding entries add exact zeros under either law; the near loop's last
             // step may take up to U - 1 far entries, which the full law treats exactly
             const int nru = (nr + U - 1) / U * U;
@@ -1009,11 +1043,7 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
     int *tabs = reinterpret_cast<int *>(w0 + (ADJ ? 4 : 2) * B + (COMP ? 192 : 0));
     int *tstart = tabs, *tpre = tabs + 128;
     unsigned char *tslot = reinterpret_cast<unsigned char *>(tabs + 256);
-    const int n_items = n_items_p[0];
-    const int n_heavy = min(n_items_p[1], n_items);
-    // two queues: heavy items [0, n_heavy) and light items [n_heavy, n_items); a warp
-    // starts on one and moves to the other once it is empty
-    int q = (warp < NF_LIGHT_WARPS * static_cast<int>(blockDim.x >> 5) / 8) ? 1 : 0;
+    const int n_items = *n_items_p;
     long long life0 = 0;
     unsigned long long wall0 = 0;
     if (prof) {
@@ -1021,21 +1051,10 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
         wall0 = global_ns();
     }
     for (;;) {
-        int it = -1;
-        if (lane == 0) {
-            for (int k = 0; k < 2 && it < 0; ++k) {
-                if (q == 0) {
-                    const int t = atomicAdd(queue, 1);
-                    if (t < n_heavy) it = t;
-                } else {
-                    const int t = n_heavy + atomicAdd(queue + 1, 1);
-                    if (t < n_items) it = t;
-                }
-                if (it < 0) q ^= 1;
-            }
-        }
+        int it = 0;
+        if (lane == 0) it = atomicAdd(queue, 1);
         it = __shfl_sync(kFull, it, 0);
-        if (it < 0) break;
+        if (it >= n_items) break;
         const Item item = items[it];
         const BoxDev &bx = boxes[item_box(item)];
         const int cnt = item_count(item);

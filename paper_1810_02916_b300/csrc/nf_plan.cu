@@ -355,8 +355,6 @@ __global__ void partition_scatter(const Item *__restrict__ items, int *__restric
     out[item_is_light(it) ? n_heavy + (i - h) : h] = it;
 }
 
-__global__ void copy_count(int *n_items) { n_items[1] = n_items[0]; }
-
 }  // namespace
 
 cudaError_t partition_light(const Item *items_in, int *n_items, int cap, int *flags, void *scan_temp,
@@ -367,12 +365,6 @@ cudaError_t partition_light(const Item *items_in, int *n_items, int cap, int *fl
     cudaError_t e = exclusive_scan_i32(flags, flags, m, scan_temp, st);
     if (e != cudaSuccess) return e;
     partition_scatter<<<nblocks(m, 256), 256, 0, st>>>(items_in, n_items, flags, items_out);
-    return cudaGetLastError();
-}
-
-cudaError_t all_items_heavy(int *n_items, cudaStream_t st)
-{
-    copy_count<<<1, 1, 0, st>>>(n_items);
     return cudaGetLastError();
 }
 
