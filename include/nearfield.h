@@ -318,15 +318,42 @@ int nf_profile_read(nf_t *nf, int64_t *launches, double *ms);
 int nf_profile_classes(nf_t *nf, uint64_t *out, int n_out);
 
 /*
- * nf_set_shape / nf_tune -- launch shape of the pair kernel: warps per block
- * (1..8) and sources staged per round (128 or 256).  nf_tune times every
- * candidate on this machine's particles (a few pair passes), keeps the fastest
- * and caches it per device and occupancy signature for later boxes (in
- * memory, and in the text file named by the NF_TUNE_CACHE environment
- * variable when it is set, so later processes reuse it);
- * report (may be NULL) receives a one-line summary.  Synchronises.
+ * nf_set_shape -- launch shape of the pair kernel: warps per block (1..8) and
+ * sources staged per round (128 or 256).
  */
 int nf_set_shape(nf_t *nf, int warps, int stage);
+
+/*
+ * nf_set_tiling -- how each cell's sinks are cut into work items (sink tiles)
+ * and how long items are split.  A cell of n particles gives floor(n / 128)
+ * tiles of 128 sinks (4 per lane); the remainder r (0 < r < 128) becomes one
+ * tile of r sinks if r > c4; otherwise a piece of 64 sinks is taken while
+ * r >= 64 and the rest becomes one tile (2 sinks per lane) if r > c2;
+ * otherwise a piece of 32 while r >= 32 and one tile (1 per lane) if r > c1;
+ * otherwise a piece of 16 while r > 16 and the rest (<= 16 sinks, with the
+ * sources split over the lanes).  64 <= c4 <= 128, 32 <= c2 <= 64,
+ * 16 <= c1 <= 32.  Items whose neighbourhood is long against the whole pass
+ * are cut into source pieces of at least split_floor sources
+ * (128 <= split_floor <= 2^20).  Default 96 / 64 / 32 / 1024.  Results change
+ * only by rounding.  Re-plans the box (synchronises).  NF_EINVAL otherwise.
+ */
+int nf_set_tiling(nf_t *nf, int c4, int c2, int c1, int split_floor);
+
+/* nf_get_tuning -- out6 = {warps, stage, c4, c2, c1, split_floor} in use. */
+int nf_get_tuning(const nf_t *nf, int32_t *out6);
+
+/*
+ * nf_tune -- the autotuner: times candidate sink tilings and split floors
+ * (nf_set_tiling) at the default launch shape, then candidate launch shapes
+ * (nf_set_shape) at the best tiling, on this machine's particles (a few pair
+ * passes each), and keeps the fastest.  Results are cached per device,
+ * accumulation, pair law, cut-off, size class and occupancy signature (the
+ * share of particles in cells of each power-of-two occupancy), in memory and
+ * in the text file named by the NF_TUNE_CACHE environment variable when it is
+ * set, so later boxes and processes with the same signature reuse them.  The
+ * box is left with one complete force pass in its FP64 sums.  report (may be
+ * NULL) receives a one-line summary ("cached" for a cache hit).  Synchronises.
+ */
 int nf_tune(nf_t *nf, char *report, int report_len);
 
 /*

@@ -31,7 +31,7 @@ EXPORTS = [
     "nf_get_forces64", "nf_kick_drift", "nf_vjp", "nf_forces_batched", "nf_profile", "nf_profile_read",
     "nf_set_shape", "nf_tune", "nf_forces_noalloc", "nf_set_softening", "nf_spline_eps_from_plummer",
     "nf_choose_dt", "nf_multipoles", "nf_set_cutoff", "nf_generation", "nf_fail_allocations",
-    "nf_profile_classes",
+    "nf_profile_classes", "nf_set_tiling", "nf_get_tuning",
 ]
 
 
@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
             "nf_generation": ([p, ctypes.POINTER(ctypes.c_uint64)], i),
             "nf_fail_allocations": ([i64, i64], i),
             "nf_profile_classes": ([p, p, i], i),
+            "nf_set_tiling": ([p, i, i, i, i], i),
+            "nf_get_tuning": ([p, p], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -316,9 +318,20 @@ class NearField:
     def set_shape(self, warps: int, stage: int):
         self._call("nf_set_shape", int(warps), int(stage))
 
+    def set_tiling(self, c4: int, c2: int, c1: int, split_floor: int):
+        """Sink tiling of the work items and the split floor (see nf_set_tiling)."""
+        self._call("nf_set_tiling", int(c4), int(c2), int(c1), int(split_floor))
+
+    def tuning(self) -> dict:
+        """Launch shape and sink tiling in use."""
+        out = np.zeros(6, np.int32)
+        self._call("nf_get_tuning", _ptr(out))
+        return dict(warps=int(out[0]), stage=int(out[1]), c4=int(out[2]), c2=int(out[3]), c1=int(out[4]),
+                    split_floor=int(out[5]))
+
     def tune(self) -> str:
-        buf = ctypes.create_string_buffer(512)
-        self._call("nf_tune", buf, 512)
+        buf = ctypes.create_string_buffer(2048)
+        self._call("nf_tune", buf, 2048)
         return buf.value.decode()
 
 

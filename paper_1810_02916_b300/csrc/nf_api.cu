@@ -42,10 +42,12 @@ struct nf_box {
     int acc_mode = NF_ACC_COMPENSATED;
     int softening = NF_SPLINE;
     PairShape shape{8, 128, 0};
+    nf::TilePolicy tiles = nf::kDefaultTiles;
 
     int64_t n = 0, cap = 0, item_cap = 0, split_cap = 0;   // split_cap: items after source splitting
     bool have_particles = false, have_forces = false;
-    uint64_t generation = 0;
+    uint64_t generation = 0;          // changes with the particles
+    uint64_t plan_gen = 0;            // changes with every re-plan (particles, cut-off, tiling)
 
     // particle state, storage order
     float4 *pos = nullptr, *vel = nullptr;
@@ -80,6 +82,7 @@ struct nf_box {
     int reduce_cap = 0;
     void *dt_tmp = nullptr;           // time-step reductions
     unsigned long long *pairs = nullptr;
+    unsigned long long *hist = nullptr;   // occupancy signature for the tuner's cache key
     BoxDev *d_box = nullptr;
     BoxDev h_box{};                   // host mirror of *d_box
     bool box_dirty = true;
@@ -283,13 +286,6 @@ int ensure_capacity(nf_t *nf, int64_t n)
     return NF_OK;
 }
 
-// shortest source piece of a split item (the per-piece cost of the neighbour
-// table and the partial write stays below a few percent)
-#ifndef NF_SPLIT_FLOOR
-#define NF_SPLIT_FLOOR 1024
-#endif
-constexpr int kSplitFloor = NF_SPLIT_FLOOR;
-
 int key_bits(int ncell)
 {
     int b = 1;
@@ -373,11 +369,11 @@ int plan(nf_t *nf)
     NF_CK(nf::zero_device_int(nf->n_raw, nf->stream));
     for (int cls = 0; cls < nf::kClasses; ++cls)
         NF_CK(nf::plan_items_class(nf->cell_start, lane_nbr, nf->ncell, 0, cls, nf->items_raw, nf->n_raw, nf->counts,
-                                   nf->offsets, nf->scan_tmp, nf->stream));
+                                   nf->offsets, nf->scan_tmp, nf->tiles, nf->stream));
     NF_CK(nf::plan_lane_items(nf->cell_start, lane_nbr, nf->cpd, 0, nf->items_raw, nf->n_raw, nf->counts,
                               nf->offsets, nf->scan_tmp, nf->stream));
     NF_CK(nf::split_items(nf->items_raw, nf->n_raw, static_cast<int>(nf->item_cap), nf->nbr_ptr, nf->pairs, nf->wf,
-                          kSplitFloor, nf->split_k, nf->split_p, nf->split_r, nf->split_scan, nf->items,
+                          nf->tiles.split_floor, nf->split_k, nf->split_p, nf->split_r, nf->split_scan, nf->items,
                           nf->n_items, nf->pieces, nf->reduces, nf->n_reduce, nf->stream));
     // heavy items first, light ones after
     NF_CK(nf::partition_light(nf->items, nf->n_items, static_cast<int>(nf->split_cap), nf->split_k, nf->split_scan,
@@ -386,6 +382,7 @@ int plan(nf_t *nf)
     if (nf->cut_nmin > 0)
         NF_CK(nf::plan_dense_cells(nf->cell_start, nf->ncell, nf->cut_nmin, nf->dslot, nf->dense_cells, nf->n_dense,
                                    nf->counts, nf->offsets, nf->scan_tmp, nf->stream));
+    nf->plan_gen = ++g_generation;
     return NF_OK;
 }
 
@@ -482,11 +479,16 @@ int produce_out(nf_t *nf, void *dst, size_t bytes, F produce)
 }
 
 std::mutex g_tune_mu;
-std::map<std::string, PairShape> g_tune_cache;
+struct Tuned {
+    PairShape shape;
+    nf::TilePolicy tiles;
+};
+std::map<std::string, Tuned> g_tune_cache;
 bool g_tune_file_loaded = false;
 
 // Tuning results persist across processes in the text file named by
-// NF_TUNE_CACHE (one "key<TAB>warps<TAB>stage" line per entry), if set.
+// NF_TUNE_CACHE (one "key<TAB>warps<TAB>stage<TAB>c4<TAB>c2<TAB>c1<TAB>split_floor"
+// line per entry), if set.
 void tune_file_load()
 {
     if (g_tune_file_loaded) return;
@@ -500,20 +502,24 @@ void tune_file_load()
         char *t1 = std::strchr(line, '\t');
         if (!t1) continue;
         *t1 = 0;
-        int w = 0, b = 0;
-        if (std::sscanf(t1 + 1, "%d\t%d", &w, &b) == 2 && w >= 1 && w <= 8 && (b == 128 || b == 256))
-            g_tune_cache[line] = PairShape{w, b, 0};
+        Tuned t{};
+        if (std::sscanf(t1 + 1, "%d\t%d\t%d\t%d\t%d\t%d", &t.shape.warps, &t.shape.stage, &t.tiles.c4, &t.tiles.c2,
+                        &t.tiles.c1, &t.tiles.split_floor) == 6 &&
+            t.shape.warps >= 1 && t.shape.warps <= 8 && (t.shape.stage == 128 || t.shape.stage == 256) &&
+            nf::tile_policy_valid(t.tiles))
+            g_tune_cache[line] = t;
     }
     std::fclose(f);
 }
 
-void tune_file_append(const std::string &key, PairShape sh)
+void tune_file_append(const std::string &key, const Tuned &t)
 {
     const char *path = std::getenv("NF_TUNE_CACHE");
     if (!path || !*path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s\t%d\t%d\n", key.c_str(), sh.warps, sh.stage);
+    std::fprintf(f, "%s\t%d\t%d\t%d\t%d\t%d\t%d\n", key.c_str(), t.shape.warps, t.shape.stage, t.tiles.c4, t.tiles.c2,
+                 t.tiles.c1, t.tiles.split_floor);
     std::fclose(f);
 }
 
@@ -607,7 +613,7 @@ void nf_destroy(nf_t *nf)
     dfree(nf->dslot); dfree(nf->dense_cells); dfree(nf->n_dense); dfree(nf->mpole); dfree(nf->nbr_all);
     if (nf->scan_tmp) cudaFree(nf->scan_tmp);
     dfree(nf->n_items); dfree(nf->queue); dfree(nf->err); dfree(nf->pairs); dfree(nf->d_box);
-    dfree(nf->n_raw); dfree(nf->n_reduce); dfree(nf->nbr_ptr);
+    dfree(nf->n_raw); dfree(nf->n_reduce); dfree(nf->nbr_ptr); dfree(nf->hist);
     if (nf->dt_tmp) cudaFree(nf->dt_tmp);
     dfree(nf->prof_cls);
     if (nf->stage.p) cudaFree(nf->stage.p);
@@ -1046,67 +1052,164 @@ int nf_set_shape(nf_t *nf, int warps, int stage)
     return NF_OK;
 }
 
+int nf_set_tiling(nf_t *nf, int c4, int c2, int c1, int split_floor)
+{
+    int rc = check_box(nf);
+    if (rc) return rc;
+    const nf::TilePolicy t{c4, c2, c1, split_floor};
+    if (!nf::tile_policy_valid(t))
+        return fail(nf, NF_EINVAL, "tiling needs 64 <= c4 <= 128, 32 <= c2 <= 64, 16 <= c1 <= 32, "
+                                   "128 <= split_floor <= 2^20");
+    nf->tiles = t;
+    if (nf->have_particles) {
+        if ((rc = plan(nf))) return rc;
+        NF_CK(cudaStreamSynchronize(nf->stream));
+    }
+    return NF_OK;
+}
+
+int nf_get_tuning(const nf_t *nf, int32_t *out6)
+{
+    if (!nf || !out6) return NF_EINVAL;
+    out6[0] = nf->shape.warps;
+    out6[1] = nf->shape.stage;
+    out6[2] = nf->tiles.c4;
+    out6[3] = nf->tiles.c2;
+    out6[4] = nf->tiles.c1;
+    out6[5] = nf->tiles.split_floor;
+    return NF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// ms per launch of the pair kernel on the current plan and shape (1 untimed + 2 timed launches)
+int time_pair(nf_t *nf, cudaEvent_t a, cudaEvent_t b, float *ms)
+{
+    int rc;
+    if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
+    NF_CK(cudaEventRecord(a, nf->stream));
+    for (int r = 0; r < 2; ++r)
+        if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
+    NF_CK(cudaEventRecord(b, nf->stream));
+    NF_CK(cudaEventSynchronize(b));
+    float t = 0;
+    NF_CK(cudaEventElapsedTime(&t, a, b));
+    *ms = t / 2;
+    return NF_OK;
+}
+
+// Cache key of a box: device, accumulation, law, cut-off, size class and its occupancy
+// signature (the share of particles in cells of occupancy 2^b..2^(b+1)-1, b = 0..17, in
+// sixteenths), so boxes with different clustering are tuned separately.
+int tune_key(nf_t *nf, std::string *key)
+{
+    cudaDeviceProp prop;
+    NF_CK(cudaGetDeviceProperties(&prop, nf->device));
+    int rc;
+    if (!nf->hist && (rc = dalloc(nf, &nf->hist, sizeof(unsigned long long) * nf::kHistBins))) return rc;
+    unsigned long long h[nf::kHistBins] = {};
+    NF_CK(nf::occupancy_hist(nf->cell_start, nf->ncell, nf->hist, nf->stream));
+    NF_CK(cudaMemcpyAsync(h, nf->hist, sizeof(h), cudaMemcpyDeviceToHost, nf->stream));
+    NF_CK(cudaStreamSynchronize(nf->stream));
+    std::string sig;
+    const double n = nf->n > 0 ? static_cast<double>(nf->n) : 1.0;
+    for (int b = 0; b < nf::kHistBins; ++b) sig += "0123456789abcdefg"[static_cast<int>(std::lround(16.0 * h[b] / n))];
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= nf->n) ++lg;
+    char k[256];
+    std::snprintf(k, sizeof(k), "%s|acc=%d|soft=%d|cut=%lld|log2n=%d|occ=%s", prop.name, nf->acc_mode, nf->softening,
+                  static_cast<long long>(nf->cut_nmin), lg, sig.c_str());
+    *key = k;
+    return NF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int nf_tune(nf_t *nf, char *report, int report_len)
 {
     int rc = check_box(nf);
     if (rc) return rc;
     if (!nf->have_particles) return fail(nf, NF_ESTATE, "no particles loaded");
-    char key[160];
-    cudaDeviceProp prop;
-    NF_CK(cudaGetDeviceProperties(&prop, nf->device));
-    std::snprintf(key, sizeof(key), "%s|cpd=%d|n=%lld|acc=%d|soft=%d", prop.name, nf->cpd,
-                  static_cast<long long>(nf->n), nf->acc_mode, nf->softening);
-    std::string summary;
+    std::string key, summary;
+    if ((rc = tune_key(nf, &key))) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_file_load();
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            nf->shape = it->second;
+            nf->shape = it->second.shape;
+            nf->tiles = it->second.tiles;
             summary = "cached";
         }
     }
-    if (summary.empty() && nf->n > 0) {
-        const PairShape cand[] = {{4, 128, 0}, {8, 128, 0}, {4, 256, 0}, {8, 256, 0}, {2, 128, 0}};
+    if (!summary.empty()) {
+        if ((rc = plan(nf))) return rc;
+    } else if (nf->n > 0) {
+        // 1. the sink tiling (remainder decomposition) and the split floor at the default launch
+        // shape, 2. the launch shape at the best tiling
+        const nf::TilePolicy tcand[] = {nf::kDefaultTiles,    {96, 40, 18, 1024}, {80, 48, 24, 1024},
+                                        {112, 40, 20, 1024},  {96, 40, 18, 512},  {96, 40, 18, 2048}};
+        const PairShape scand[] = {{8, 128, 0}, {4, 128, 0}, {8, 256, 0}, {4, 256, 0}, {2, 128, 0}};
         cudaEvent_t a, b;
         NF_CK(cudaEventCreate(&a));
         NF_CK(cudaEventCreate(&b));
-        float best = 1e30f;
-        PairShape best_s = nf->shape;
         const bool prof = nf->profile;
         nf->profile = false;
+        Tuned best{PairShape{8, 128, 0}, nf::kDefaultTiles};
+        float best_ms = 1e30f;
+        char part[128];
         if ((rc = upload_box(nf, nullptr, nf->acc64, nullptr))) return rc;
-        for (const PairShape &s : cand) {
-            if (nf::pair_max_blocks_per_sm(nf->acc_mode == NF_ACC_COMPENSATED, 0, nf->softening, s) < 1) continue;
-            nf->shape = s;
-            if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
-            NF_CK(cudaEventRecord(a, nf->stream));
-            for (int r = 0; r < 2; ++r)
-                if ((rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0))) return rc;
-            NF_CK(cudaEventRecord(b, nf->stream));
-            NF_CK(cudaEventSynchronize(b));
-            float t = 0;
-            NF_CK(cudaEventElapsedTime(&t, a, b));
-            char part[96];
-            std::snprintf(part, sizeof(part), "%dx%d:%.3fms ", s.warps, s.stage, t / 2);
+        nf->shape = best.shape;
+        for (const nf::TilePolicy &t : tcand) {
+            nf->tiles = t;
+            float ms = 0;
+            if ((rc = plan(nf)) || (rc = time_pair(nf, a, b, &ms))) return rc;
+            std::snprintf(part, sizeof(part), "tiles %d/%d/%d/%d:%.3fms ", t.c4, t.c2, t.c1, t.split_floor, ms);
             summary += part;
-            if (t < best) {
-                best = t;
-                best_s = s;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.tiles = t;
+            }
+        }
+        nf->tiles = best.tiles;
+        if ((rc = plan(nf))) return rc;
+        best_ms = 1e30f;
+        for (const PairShape &sh : scand) {
+            if (nf::pair_max_blocks_per_sm(nf->acc_mode == NF_ACC_COMPENSATED, 0, nf->softening, sh) < 1) continue;
+            nf->shape = sh;
+            float ms = 0;
+            if ((rc = time_pair(nf, a, b, &ms))) return rc;
+            std::snprintf(part, sizeof(part), "shape %dx%d:%.3fms ", sh.warps, sh.stage, ms);
+            summary += part;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.shape = sh;
             }
         }
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         nf->profile = prof;
-        nf->shape = best_s;
-        nf->have_forces = true;
+        nf->shape = best.shape;
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = best_s;
-        tune_file_append(key, best_s);
-        char part[64];
-        std::snprintf(part, sizeof(part), "-> %dx%d", best_s.warps, best_s.stage);
+        g_tune_cache[key] = best;
+        tune_file_append(key, best);
+        std::snprintf(part, sizeof(part), "-> %dx%d tiles %d/%d/%d/%d", best.shape.warps, best.shape.stage,
+                      best.tiles.c4, best.tiles.c2, best.tiles.c1, best.tiles.split_floor);
         summary += part;
     }
+    // leave one complete force pass (partials reduced) in the box's FP64 sums
+    if (nf->n > 0) {
+        if ((rc = upload_box(nf, nullptr, nf->acc64, nullptr)) ||
+            (rc = launch_forces(nf, nf->d_box, nf->items, nf->n_items, nf->queue, 0)))
+            return rc;
+        NF_CK(nf::reduce_partials(nf->d_box, nf->reduces, nf->n_reduce, nf->reduce_cap, 0, nf->stream));
+        NF_CK(cudaStreamSynchronize(nf->stream));
+    }
+    nf->have_forces = true;
     if (report && report_len > 0) std::snprintf(report, static_cast<size_t>(report_len), "%s", summary.c_str());
     return NF_OK;
 }
@@ -1218,7 +1321,7 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
     std::lock_guard<std::mutex> lk(g_batch_mu);
     Batch &B = g_batch;
     bool same = B.device == nf->device && static_cast<int>(B.boxes.size()) == nbox;
-    for (int b = 0; same && b < nbox; ++b) same = B.boxes[b] == boxes[b] && B.gens[b] == boxes[b]->generation;
+    for (int b = 0; same && b < nbox; ++b) same = B.boxes[b] == boxes[b] && B.gens[b] == boxes[b]->plan_gen;
     if (!same) {
         // (re)plan: one item list over all boxes, class-major (largest cells first), then split
         cudaStreamSynchronize(nf->stream);
@@ -1244,7 +1347,7 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
             for (int b = 0; b < nbox; ++b)
                 NF_CK(nf::plan_items_class(boxes[b]->cell_start, boxes[b]->nbr, boxes[b]->ncell, b, cls, B.items_raw,
                                            B.n_raw, boxes[b]->counts, boxes[b]->offsets, boxes[b]->scan_tmp,
-                                           nf->stream));
+                                           boxes[b]->tiles, nf->stream));
         for (int b = 0; b < nbox; ++b)
             NF_CK(nf::plan_lane_items(boxes[b]->cell_start, boxes[b]->nbr, boxes[b]->cpd, b, B.items_raw, B.n_raw,
                                       boxes[b]->counts, boxes[b]->offsets, boxes[b]->scan_tmp, nf->stream));
@@ -1252,7 +1355,7 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
         NF_CK(cudaMemcpyAsync(B.pair_ptrs, prs.data(), sizeof(void *) * nbox, cudaMemcpyHostToDevice, nf->stream));
         NF_CK(nf::sum_pair_counts(B.pair_ptrs, nbox, B.total, nf->stream));
         NF_CK(nf::split_items(B.items_raw, B.n_raw, static_cast<int>(B.raw_cap), B.nbr_ptrs, B.total, nf->wf,
-                              kSplitFloor, B.split_k, B.split_p, B.split_r, B.split_scan, B.items, B.n_items, B.pieces,
+                              nf->tiles.split_floor, B.split_k, B.split_p, B.split_r, B.split_scan, B.items, B.n_items, B.pieces,
                               B.reduces, B.n_reduce, nf->stream));
         NF_CK(nf::partition_light(B.items, B.n_items, static_cast<int>(B.split_cap), B.split_k, B.split_scan,
                                   B.items_raw, nf->stream));
@@ -1260,7 +1363,7 @@ extern "C" int nf_forces_batched(nf_t *const *boxes, int nbox, float *const *acc
         NF_CK(cudaStreamSynchronize(nf->stream));   // the host vectors above must outlive their copies
         B.boxes.assign(boxes, boxes + nbox);
         B.gens.resize(nbox);
-        for (int b = 0; b < nbox; ++b) B.gens[b] = boxes[b]->generation;
+        for (int b = 0; b < nbox; ++b) B.gens[b] = boxes[b]->plan_gen;
         B.h_desc.assign(nbox, BoxDev{});
         NF_CK(cudaMemsetAsync(B.d_desc, 0, sizeof(BoxDev) * nbox, nf->stream));
     }

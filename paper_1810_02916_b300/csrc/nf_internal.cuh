@@ -96,6 +96,26 @@ constexpr int kCutWords = 10;
 // 125-cell neighbourhood may (kLaneMaxT), so no lane item has a dense cell in reach
 constexpr int kCutMinN = 1024;
 
+// How a cell's sinks are cut into work items (its sink tiles): floor(n / 128)
+// full tiles of 128 sinks, then the remainder r (0 < r < 128): one tile of r
+// sinks if r > c4 (4 sinks per lane); otherwise a piece of 64 while r >= 64,
+// then one tile of r if r > c2 (2 per lane); otherwise a piece of 32 while
+// r >= 32, then one tile of r if r > c1 (1 per lane); otherwise a piece of 16
+// while r > 16, and the rest (<= 16 sinks, the sources split over the lanes).
+// c4 in [64, 128], c2 in [32, 64], c1 in [16, 32].  Every piece but the last
+// has at least 16 sinks, so a cell of n particles makes at most 1 + n / 16
+// items.  split_floor: the shortest source piece of a split item.
+struct TilePolicy {
+    int c4, c2, c1;
+    int split_floor;
+};
+constexpr TilePolicy kDefaultTiles{96, 64, 32, 1024};
+__host__ __device__ inline bool tile_policy_valid(const TilePolicy &p)
+{
+    return p.c4 >= 64 && p.c4 <= 128 && p.c2 >= 32 && p.c2 <= 64 && p.c1 >= 16 && p.c1 <= 32 &&
+           p.split_floor >= 128 && p.split_floor <= (1 << 20);
+}
+
 // Occupancy classes used to order the work queue (largest cells first).
 constexpr int kClasses = 5;
 __host__ __device__ inline int occupancy_class(int n)
@@ -154,7 +174,7 @@ cudaError_t count_keys(const uint32_t *keys, int n, int *counts, cudaStream_t st
 // nbr_all in cut-off mode), which decides the cells left to lane items.
 cudaError_t plan_items_class(const int *cell_start, const int *nbr, int ncell, int box_index, int cls, Item *items,
                              int *n_items, int *scratch_counts, int *scratch_offsets, void *scan_temp,
-                             cudaStream_t st);
+                             TilePolicy pol, cudaStream_t st);
 // Lane items of one box (see lane_cell), appended at items[*n_items] after
 // every occupancy class.  Scratch: cpd^2 + 1 ints each.
 cudaError_t plan_lane_items(const int *cell_start, const int *nbr, int cpd, int box_index, Item *items, int *n_items,
@@ -174,6 +194,10 @@ cudaError_t split_items(const Item *items_in, const int *n_in, int item_cap, con
 // cap + 1 ints of scratch, scan_temp: scan_temp_bytes(cap + 1).
 cudaError_t partition_light(const Item *items_in, int *n_items, int cap, int *flags, void *scan_temp,
                             Item *items_out, cudaStream_t st);
+// Occupancy signature of a box: hist[b] (b = 0..kHistBins-1) = particles in
+// cells whose occupancy n has floor(log2(n)) = b (the last bin takes the rest).
+constexpr int kHistBins = 18;
+cudaError_t occupancy_hist(const int *cell_start, int ncell, unsigned long long *hist, cudaStream_t st);
 // *out = sum of the n values at ptrs[0..n)
 cudaError_t sum_pair_counts(const unsigned long long *const *ptrs, int n, unsigned long long *out, cudaStream_t st);
 cudaError_t reduce_partials(const BoxDev *boxes, const Reduce *reduces, const int *n_reduce, int max_reduce,

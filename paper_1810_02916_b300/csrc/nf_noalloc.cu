@@ -159,7 +159,8 @@ extern "C" int nf_forces_noalloc(int cpd, double eps, double box, const int32_t 
     NA_CK(nf::neighbour_pairs(cell_start, cpd, 0, pairs, counts, offsets, nbr, nullptr, st));
     NA_CK(nf::zero_device_int(n_items, st));
     for (int cls = 0; cls < nf::kClasses; ++cls)
-        NA_CK(nf::plan_items_class(cell_start, nbr, ncell, 0, cls, items, n_items, counts, offsets, scan_tmp, st));
+        NA_CK(nf::plan_items_class(cell_start, nbr, ncell, 0, cls, items, n_items, counts, offsets, scan_tmp,
+                                   nf::kDefaultTiles, st));
     NA_CK(nf::plan_lane_items(cell_start, nbr, cpd, 0, items, n_items, counts, offsets, scan_tmp, st));
     const double inv_w = static_cast<double>(cpd) / box;
     const double ec = eps * inv_w;

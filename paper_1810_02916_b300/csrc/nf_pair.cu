@@ -75,6 +75,9 @@ namespace {
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
+#ifndef NF_LANE_UNROLL
+#define NF_LANE_UNROLL 4   // sources per unrolled step of a lane item (independent loads in flight)
+#endif
 #ifndef NF_PAIR_UNROLL
 #define NF_PAIR_UNROLL 2   // source pairs per unrolled step on lanes holding one sink
 #endif
@@ -974,20 +977,31 @@ __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
                     pair_adjoint<SOFT>(q, __ldg(bx.cot + j), p.x, p.y, p.z, w.x, w.y, w.z, px, py, pz, a0, a1, a2,
                                        eps2);
                 }
-            } else if (NF_LANE_FAR_LAW && far_col) {
-                for (int j = j0; j < j1; ++j) {
-                    const float4 q0 = __ldg(bx.pos + j);
-                    const int dz = dz0 + (j >= b1) + (j >= b2) + (j >= b3) + (j >= b4);
-                    // d = x_j + D - x_i, exact (each sum lies on the 2^-22 grid)
-                    const float ddx = q0.x + ox, ddy = q0.y + oy, ddz = q0.z + (static_cast<float>(dz) - p.z);
-                    tail_newton(ddx, ddy, ddz, fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx)), px, py, pz);
-                }
             } else {
-                for (int j = j0; j < j1; ++j) {
-                    const float4 q0 = __ldg(bx.pos + j);
-                    const int dz = dz0 + (j >= b1) + (j >= b2) + (j >= b3) + (j >= b4);
-                    const float4 q = make_float4(q0.x + fx, q0.y + fy, q0.z + static_cast<float>(dz), 0.f);
-                    pair_force<SOFT>(q, p.x, p.y, p.z, px, py, pz, a0, a1, a2, eps2);
+                // NF_LANE_UNROLL sources per step, their loads issued together; entries past the
+                // run become far-away padding (exact zeros under either law)
+                constexpr int LU = NF_LANE_UNROLL;
+                const bool newton = NF_LANE_FAR_LAW && far_col;
+                for (int j = j0; j < j1; j += LU) {
+                    float4 q0[LU];
+#pragma unroll
+                    for (int u = 0; u < LU; ++u)
+                        q0[u] = (u == 0 || j + u < j1) ? __ldg(bx.pos + j + u) : make_float4(kFar, kFar, kFar, 0.f);
+#pragma unroll
+                    for (int u = 0; u < LU; ++u) {
+                        const int ju = j + u;
+                        const int dz = dz0 + (ju >= b1) + (ju >= b2) + (ju >= b3) + (ju >= b4);
+                        if (newton) {
+                            // d = x_j + D - x_i, exact (each sum lies on the 2^-22 grid)
+                            const float ddx = q0[u].x + ox, ddy = q0[u].y + oy,
+                                        ddz = q0[u].z + (static_cast<float>(dz) - p.z);
+                            tail_newton(ddx, ddy, ddz, fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx)), px, py, pz);
+                        } else {
+                            const float4 q = make_float4(q0[u].x + fx, q0[u].y + fy, q0[u].z + static_cast<float>(dz),
+                                                         0.f);
+                            pair_force<SOFT>(q, p.x, p.y, p.z, px, py, pz, a0, a1, a2, eps2);
+                        }
+                    }
                 }
             }
             if (COMP) {

@@ -16,6 +16,8 @@
 // one sink per lane, which spares the tail one warp-wide setup per cell.
 // Nothing here leaves the device: the item count stays in device memory and
 // is read by the pair kernel, so planning needs no host synchronisation.
+#include <algorithm>
+
 #include "nf_internal.cuh"
 
 namespace nf {
@@ -23,30 +25,39 @@ namespace {
 
 inline int nblocks(int64_t n, int per) { return static_cast<int>((n + per - 1) / per); }
 
-// sizes of the remainder pieces of r (0 < r < 128); returns how many (<= 4)
-__device__ __forceinline__ int remainder_pieces(int r, int *out)
+// sizes of the remainder pieces of r (0 < r < 128) under the tile policy (see
+// TilePolicy); returns how many (<= 4)
+__device__ __forceinline__ int remainder_pieces(int r, const TilePolicy &pol, int *out)
 {
     int k = 0;
-    if (r > 96) {
+    if (r > pol.c4) {
         out[k++] = r;
         return k;
     }
     if (r >= 64) { out[k++] = 64; r -= 64; }
+    if (r > pol.c2) {
+        out[k++] = r;
+        return k;
+    }
     if (r >= 32) { out[k++] = 32; r -= 32; }
+    if (r > pol.c1) {
+        out[k++] = r;
+        return k;
+    }
     if (r > 16) { out[k++] = 16; r -= 16; }
     if (r > 0) out[k++] = r;
     return k;
 }
 
-__device__ __forceinline__ int items_of_cell(int n)
+__device__ __forceinline__ int items_of_cell(int n, const TilePolicy &pol)
 {
     int tmp[4];
     const int r = n % kTile;
-    return n / kTile + (r ? remainder_pieces(r, tmp) : 0);
+    return n / kTile + (r ? remainder_pieces(r, pol, tmp) : 0);
 }
 
 __global__ void class_counts(const int *__restrict__ cell_start, const int *__restrict__ nbr, int ncell, int cls,
-                             int *__restrict__ counts)
+                             TilePolicy pol, int *__restrict__ counts)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c > ncell) return;
@@ -55,11 +66,11 @@ __global__ void class_counts(const int *__restrict__ cell_start, const int *__re
         return;
     }
     const int n = cell_start[c + 1] - cell_start[c];
-    counts[c] = (!lane_cell(n, nbr[c]) && occupancy_class(n) == cls) ? items_of_cell(n) : 0;
+    counts[c] = (!lane_cell(n, nbr[c]) && occupancy_class(n) == cls) ? items_of_cell(n, pol) : 0;
 }
 
 __global__ void emit_items(const int *__restrict__ cell_start, const int *__restrict__ nbr, int ncell, int cls,
-                           int box, const int *__restrict__ offsets, const int *__restrict__ base_p,
+                           int box, TilePolicy pol, const int *__restrict__ offsets, const int *__restrict__ base_p,
                            Item *__restrict__ items)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -80,7 +91,7 @@ __global__ void emit_items(const int *__restrict__ cell_start, const int *__rest
     const int r = n % kTile;
     if (r) {
         int sz[4];
-        const int k = remainder_pieces(r, sz);
+        const int k = remainder_pieces(r, pol, sz);
         for (int q = 0; q < k; ++q, ++out) {
             it.sink_begin = begin;
             it.box_count = (box << 16) | sz[q];
@@ -355,7 +366,29 @@ __global__ void partition_scatter(const Item *__restrict__ items, int *__restric
     out[item_is_light(it) ? n_heavy + (i - h) : h] = it;
 }
 
+__global__ void hist_kernel(const int *__restrict__ cell_start, int ncell, unsigned long long *__restrict__ hist)
+{
+    __shared__ unsigned long long h[kHistBins];
+    if (threadIdx.x < kHistBins) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const int n = cell_start[c + 1] - cell_start[c];
+        if (n > 0) atomicAdd(&h[min(31 - __clz(n), kHistBins - 1)], static_cast<unsigned long long>(n));
+    }
+    __syncthreads();
+    if (threadIdx.x < kHistBins && h[threadIdx.x]) atomicAdd(hist + threadIdx.x, h[threadIdx.x]);
+}
+
 }  // namespace
+
+cudaError_t occupancy_hist(const int *cell_start, int ncell, unsigned long long *hist, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kHistBins, st);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min(1024, nblocks(ncell, 256)));
+    hist_kernel<<<blocks, 256, 0, st>>>(cell_start, ncell, hist);
+    return cudaGetLastError();
+}
 
 cudaError_t partition_light(const Item *items_in, int *n_items, int cap, int *flags, void *scan_temp,
                             Item *items_out, cudaStream_t st)
@@ -422,14 +455,14 @@ cudaError_t zero_device_int(int *p, cudaStream_t st)
 
 cudaError_t plan_items_class(const int *cell_start, const int *nbr, int ncell, int box_index, int cls, Item *items,
                              int *n_items, int *scratch_counts, int *scratch_offsets, void *scan_temp,
-                             cudaStream_t st)
+                             TilePolicy pol, cudaStream_t st)
 {
-    class_counts<<<nblocks(static_cast<int64_t>(ncell) + 1, 256), 256, 0, st>>>(cell_start, nbr, ncell, cls,
+    class_counts<<<nblocks(static_cast<int64_t>(ncell) + 1, 256), 256, 0, st>>>(cell_start, nbr, ncell, cls, pol,
                                                                                  scratch_counts);
     cudaError_t e =
         exclusive_scan_i32(scratch_counts, scratch_offsets, static_cast<int64_t>(ncell) + 1, scan_temp, st);
     if (e != cudaSuccess) return e;
-    emit_items<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, nbr, ncell, cls, box_index, scratch_offsets,
+    emit_items<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, nbr, ncell, cls, box_index, pol, scratch_offsets,
                                                     n_items, items);
     advance_base<<<1, 1, 0, st>>>(n_items, scratch_offsets, ncell);
     return cudaGetLastError();

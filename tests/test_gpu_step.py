@@ -290,7 +290,43 @@ def test_tuner_result_persists_in_the_cache_file(tmp_path):
     env = dict(os.environ, NF_TUNE_CACHE=str(cache))
     first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert first.returncode == 0, first.stderr
-    assert "->" in first.stdout and cache.exists() and cache.read_text().count("\t") == 2
+    assert "->" in first.stdout and cache.exists() and cache.read_text().count("\t") == 6
     second = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert second.returncode == 0, second.stderr
     assert second.stdout.strip() == "cached"
+
+
+TILINGS = [(96, 64, 32, 1024), (96, 40, 18, 1024), (80, 48, 24, 1024), (112, 40, 20, 1024), (96, 40, 18, 512),
+           (96, 40, 18, 2048), (64, 32, 16, 128), (128, 64, 32, 1 << 20)]
+
+
+@pytest.mark.parametrize("tiling", TILINGS, ids=["-".join(map(str, t)) for t in TILINGS])
+def test_every_tiling_matches_the_oracle(tiling):
+    """The tuner's candidate tilings (and the extremes of the allowed range) all give the
+    oracle's forces: a clustered box whose cells hold every remainder 1..127."""
+    X, _ = gen.clustered(60000, np.random.default_rng(33), 5, 0.3 / 9, 1.5 / 9)
+    nf = make_box(X, 9, 1e-3)
+    nf.set_tiling(*tiling)
+    assert nf.tuning()["c4"] == tiling[0] and nf.tuning()["split_floor"] == tiling[3]
+    acc = nf.forces()
+    b = oracle_side(X, 9)
+    ref, sa, _ = oracle.forces(b, 1e-3, with_sumabs=True)
+    s = oracle.error_stats(acc[:, :3], ref, sa)
+    assert s["rms_rel"] <= RMS_TOL and s["max_bound_ratio"] <= BOUND_K, s
+
+
+def test_tuner_keys_on_the_occupancy_profile():
+    """Two boxes of the same size but different clustering get separate tuning runs; a third box
+    with the first one's profile reuses its result."""
+    rng = np.random.default_rng(34)
+    Xu = rng.random((120000, 3))
+    Xc, _ = gen.clustered(120000, np.random.default_rng(35), 6, 0.3 / 14, 1.2 / 14)
+    a, b = make_box(Xu, 14, 1e-3), make_box(Xc, 14, 1e-3)
+    ra, rb = a.tune(), b.tune()
+    assert "->" in ra and "->" in rb and "tiles" in ra
+    c = make_box(np.random.default_rng(36).random((120000, 3)), 14, 1e-3)
+    assert c.tune() == "cached" and c.tuning() == a.tuning()
+    ref = oracle.forces(oracle_side(Xc, 14), 1e-3)
+    s = oracle.error_stats(b.forces()[:, :3], ref)
+    assert s["rms_rel"] <= RMS_TOL, s
+
