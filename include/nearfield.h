@@ -334,7 +334,7 @@ int nf_set_shape(nf_t *nf, int warps, int stage);
  * sources split over the lanes).  64 <= c4 <= 128, 32 <= c2 <= 64,
  * 16 <= c1 <= 32.  Items whose neighbourhood is long against the whole pass
  * are cut into source pieces of at least split_floor sources
- * (128 <= split_floor <= 2^20).  Default 96 / 64 / 32 / 1024.  Results change
+ * (128 <= split_floor <= 2^20).  Default 96 / 40 / 18 / 1024.  Results change
  * only by rounding.  Re-plans the box (synchronises).  NF_EINVAL otherwise.
  */
 int nf_set_tiling(nf_t *nf, int c4, int c2, int c1, int split_floor);

@@ -1151,8 +1151,8 @@ int nf_tune(nf_t *nf, char *report, int report_len)
     } else if (nf->n > 0) {
         // 1. the sink tiling (remainder decomposition) and the split floor at the default launch
         // shape, 2. the launch shape at the best tiling
-        const nf::TilePolicy tcand[] = {nf::kDefaultTiles,    {96, 40, 18, 1024}, {80, 48, 24, 1024},
-                                        {112, 40, 20, 1024},  {96, 40, 18, 512},  {96, 40, 18, 2048}};
+        const nf::TilePolicy tcand[] = {nf::kDefaultTiles,  {96, 64, 32, 1024}, {80, 48, 24, 1024},
+                                        {112, 40, 20, 1024}, {96, 40, 18, 512},  {96, 40, 18, 2048}};
         const PairShape scand[] = {{8, 128, 0}, {4, 128, 0}, {8, 256, 0}, {4, 256, 0}, {2, 128, 0}};
         cudaEvent_t a, b;
         NF_CK(cudaEventCreate(&a));

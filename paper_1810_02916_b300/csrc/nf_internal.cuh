@@ -109,7 +109,9 @@ struct TilePolicy {
     int c4, c2, c1;
     int split_floor;
 };
-constexpr TilePolicy kDefaultTiles{96, 64, 32, 1024};
+// default: the tuner's choice on the 512^3 and 256^3 clustered workloads (a remainder of
+// 19-31 or 41-63 sinks runs as one partly filled tile rather than split-mode pieces)
+constexpr TilePolicy kDefaultTiles{96, 40, 18, 1024};
 __host__ __device__ inline bool tile_policy_valid(const TilePolicy &p)
 {
     return p.c4 >= 64 && p.c4 <= 128 && p.c2 >= 32 && p.c2 <= 64 && p.c1 >= 16 && p.c1 <= 32 &&
