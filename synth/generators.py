@@ -311,15 +311,25 @@ def _tiles128(cpd: int = 40, per_cell: int = 128):
     return Workload(f"tiles{per_cell}", pos, cpd, (1.0 / n ** (1.0 / 3.0)) / 40.0, meta=dict(per_cell=per_cell))
 
 
+def _sparse2(cpd: int = 200, per_cell: int = 2):
+    """Uniform random particles at per_cell per cell on average (cpd^3 cells): almost every cell
+    is sparse, so nearly all work runs as lane items (a profiling workload)."""
+    rng = rng_for(7)
+    n = per_cell * cpd ** 3
+    return Workload(f"sparse{per_cell}", uniform(n, rng), cpd, (1.0 / n ** (1.0 / 3.0)) / 40.0,
+                    meta=dict(per_cell=per_cell))
+
+
 WORKLOADS = {
     "uniform32k": _uniform32k,
     "clustered256": _clustered,
     "zeldovich512": _zeldovich,
     "clustered64": _clustered64,
     "tiles128": _tiles128,
+    "sparse2": _sparse2,
 }
 
 
 def workload(name: str, **kw) -> Workload:
-    """Named workload: uniform32k, clustered256, zeldovich512, clustered64, tiles128."""
+    """Named workload: uniform32k, clustered256, zeldovich512, clustered64, tiles128, sparse2."""
     return WORKLOADS[name](**kw)
