@@ -47,8 +47,8 @@ ISSUE_OPS_PER_PAIR = 20    # FP32-pipe instructions per pair of the branch-free 
 # DRAM bytes (read + write) of one compensated pair-kernel launch of this workload, from the ncu
 # launch list of this workload, valid while nf_pair.cu hashes to the value below (the record
 # reports null traffic once the kernel source has changed)
-PAIR_TRAFFIC_BYTES = 9.3688e9
-PAIR_TRAFFIC_SOURCE_SHA256 = "486cb77da20fc0e7"
+PAIR_TRAFFIC_BYTES = 1.30123e10
+PAIR_TRAFFIC_SOURCE_SHA256 = "6a6500b2c88817af"
 FP32_LANES_PER_SM = 128
 
 

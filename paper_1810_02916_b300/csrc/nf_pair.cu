@@ -75,9 +75,6 @@ namespace {
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
-#ifndef NF_LANE_STAGED
-#define NF_LANE_STAGED 1   // lane items stage their columns in shared memory (0: every lane reads global memory)
-#endif
 #ifndef NF_LANE_UNROLL
 #define NF_LANE_UNROLL 4   // sources per unrolled step of a lane item (independent loads in flight)
 #endif
@@ -1029,212 +1026,12 @@ __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
         bx.acc_out[i] = make_float4(static_cast<float>(gx), static_cast<float>(gy), static_cast<float>(gz), 0.f);
 }
 
-// A lane item with its neighbourhood staged by the warp.  All sinks of the run
-// lie in one z-row of cells [g0, g0 + ng), so their 25 (dx, dy) columns are
-// shared: for each column the warp stages the particles of the union of the
-// sinks' z-windows, cells z0 - 2 .. z0 + ng + 1 (nz = ng + 4 cells, periodic),
-// into shared memory with coalesced cp.async copies (double-buffered across
-// columns), tagging every entry with the column offset (added to x and y) and
-// its cell's z offset from the run's first cell (in w).  Each lane then sums its
-// own sink's window, the union cells rz .. rz + 4 of its cell rz, reading the
-// staged entries; the z separation (x_j + dz) - x_i is formed exactly from the
-// tag.  The whole item first loads the cell table of all 25 columns at once.
-// Shared memory: ltab (1024 ints: 25 columns x (nz + 2) table words, then the
-// column's union-cell bounds), stage (2 x B float4), tslot (2 x B bytes).
-// 25 columns x (ng + 6) table words + ng + 5 bounds must fit the 1024-int region
-static_assert(26 * kLaneMaxCells + 155 <= 1024, "lane-item cell table exceeds its shared memory");
-
-template <int B, bool COMP, int SOFT>
-__device__ void run_lanes_staged(const BoxDev &bx, const Item &item, float4 *stage, int *ltab,
-                                 unsigned char *tslot, int lane)
-{
-    const int count = item_count(item);
-    const int C = bx.cpd;
-    const int *cs = bx.cell_start;
-    const int g0 = item.cell, ng = item_lane_cells(item);
-    const int z0 = g0 % C, y0 = (g0 / C) % C, x0 = g0 / (C * C);
-    const int nz = ng + 4, nw = nz + 2;   // union cells; table words per column
-    const int zs = z0 >= 2 ? z0 - 2 : z0 - 2 + C;
-    int *bnd = ltab + 25 * nw;            // the current column's union-cell bounds, nz + 1 ints
-
-    // the cell table of every column: starts of the union cells, the row's end and the
-    // last union cell's end (one memory latency for the whole item)
-    for (int t = lane; t < 25 * nw; t += 32) {
-        const int col = t / nw, k = t - col * nw;
-        int nx = x0 + col / 5 - 2, ny = y0 + col % 5 - 2;
-        nx += nx < 0 ? C : 0; nx -= nx >= C ? C : 0;
-        ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
-        const int rb = (nx * C + ny) * C;
-        int idx;
-        if (k < nz || k == nz + 1) {
-            int z = zs + (k < nz ? k : nz - 1);
-            z -= z >= C ? C : 0;
-            z -= z >= C ? C : 0;
-            idx = rb + z + (k == nz + 1 ? 1 : 0);
-        } else {
-            idx = rb + C;
-        }
-        ltab[t] = __ldg(cs + idx);
-    }
-    __syncwarp();
-
-    // union-cell bounds of column col into bnd (exclusive prefix of counts); returns the total
-    auto make_bnd = [&](int col) -> int {
-        const int *tb = ltab + col * nw;
-        int cnt[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int u = lane + 32 * h;
-            cnt[h] = 0;
-            if (u < nz) {
-                int z = zs + u;
-                z -= z >= C ? C : 0;
-                z -= z >= C ? C : 0;
-                const int end = u == nz - 1 ? tb[nz + 1] : (z == C - 1 ? tb[nz] : tb[u + 1]);
-                cnt[h] = end - tb[u];
-            }
-        }
-        int run = 0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int incl = cnt[h];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int u = lane + 32 * h;
-            if (u < nz) bnd[u] = run + incl - cnt[h];
-            run += __shfl_sync(kFull, incl, 31);
-        }
-        if (lane == 0) bnd[nz] = run;
-        __syncwarp();
-        return run;
-    };
-    // copy staged entries [base, base + B) of column col (bounds in bnd) into buf
-    auto issue = [&](int col, int base, int total, float4 *buf, unsigned char *ts) {
-        const int *tb = ltab + col * nw;
-#pragma unroll
-        for (int m = 0; m < B / 32; ++m) {
-            const int slot = m * 32 + lane;
-            const int s = base + slot;
-            if (s < total) {
-                int lo = 0, hi = nz;   // bnd[lo] <= s < bnd[hi]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (bnd[mid] <= s) lo = mid; else hi = mid;
-                }
-                cp_async16(buf + slot, bx.pos + tb[lo] + (s - bnd[lo]));
-                ts[slot] = static_cast<unsigned char>(lo);
-            }
-        }
-        cp_async_commit();
-    };
-
-    // the lane's sink and its cell's place in the run
-    const bool has = lane < count;
-    const int i = item.sink_begin + (has ? lane : 0);
-    int rz = 0;
-    for (int k = 1; k < ng; ++k) rz += __ldg(cs + g0 + k) <= i;
-    const float4 p = __ldg(bx.pos + i);
-    const float rzf = static_cast<float>(rz);
-    const float a0 = bx.a0, a1 = bx.a1, a2 = bx.a2, eps2 = bx.eps2;
-    Comp3 acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-
-    int col = 0, base = 0, total = make_bnd(0);
-    int w0 = has ? bnd[rz] : 0, w1 = has ? bnd[rz + 5] : 0;   // the lane's window in column 0
-    issue(0, 0, total, stage, tslot);
-    float px = 0.f, py = 0.f, pz = 0.f;
-    for (int k = 0;; ++k) {
-        float4 *buf = stage + (k & 1) * B;
-        unsigned char *ts = tslot + (k & 1) * B;
-        // the next chunk: the column's next B entries, or the next column's first
-        const bool more = base + B < total;
-        const int ncol = more ? col : col + 1, nbase = more ? base + B : 0;
-        int ntotal = total;
-        if (ncol < 25) {
-            if (!more) ntotal = make_bnd(ncol);
-            issue(ncol, nbase, ntotal, stage + ((k + 1) & 1) * B, tslot + ((k + 1) & 1) * B);
-            cp_async_wait_1();
-        } else {
-            cp_async_wait_0();
-        }
-        __syncwarp();
-        // tag this lane's landed entries: column offset on x and y, cell z offset in w
-        const float fx = static_cast<float>(col / 5 - 2), fy = static_cast<float>(col % 5 - 2);
-#pragma unroll
-        for (int m = 0; m < B / 32; ++m) {
-            const int slot = m * 32 + lane;
-            if (base + slot < total) {
-                float4 v = buf[slot];
-                v.x += fx;
-                v.y += fy;
-                v.w = static_cast<float>(static_cast<int>(ts[slot]) - 2);
-                buf[slot] = v;
-            }
-        }
-        __syncwarp();
-        // this lane's window within the chunk
-        const int s0 = max(w0, base) - base, s1 = min(w1, base + B) - base;
-        const bool far_col = SOFT == 0 && (col / 5 == 0 || col / 5 == 4 || col % 5 == 0 || col % 5 == 4);
-        constexpr int LU = NF_LANE_UNROLL;
-        for (int s = s0; s < s1; s += LU) {
-#pragma unroll
-            for (int u = 0; u < LU; ++u) {
-                const float4 q = (u == 0 || s + u < s1) ? buf[s + u] : make_float4(kFar, kFar, kFar, 0.f);
-                // d = x_j + D - x_i, exact: every sum lies on the 2^-22 grid below 4 in magnitude
-                const float ddx = q.x - p.x, ddy = q.y - p.y, ddz = q.z + ((q.w - rzf) - p.z);
-                if (far_col) {
-                    tail_newton(ddx, ddy, ddz, fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx)), px, py, pz);
-                } else if (SOFT == 1) {
-                    pair_force<1>(make_float4(q.x, q.y, q.z + (q.w - rzf), 0.f), p.x, p.y, p.z, px, py, pz, a0,
-                                  a1, a2, eps2);
-                } else {
-                    tail_spline(ddx, ddy, ddz, fmaf(ddz, ddz, fmaf(ddy, ddy, fmaf(ddx, ddx, FLT_MIN))), px, py, pz,
-                                a0, a1, a2);
-                }
-            }
-        }
-        __syncwarp();
-        if (!more) {
-            // the column is done: fold its partial sum
-            if (COMP) {
-                float s2, e;
-                two_sum(acc.hx, px, s2, e); acc.hx = s2; acc.lx = __fadd_rn(acc.lx, e);
-                two_sum(acc.hy, py, s2, e); acc.hy = s2; acc.ly = __fadd_rn(acc.ly, e);
-                two_sum(acc.hz, pz, s2, e); acc.hz = s2; acc.lz = __fadd_rn(acc.lz, e);
-            } else {
-                acc.hx += px; acc.hy += py; acc.hz += pz;
-            }
-            px = py = pz = 0.f;
-            if (ncol >= 25) break;
-            w0 = has ? bnd[rz] : 0;
-            w1 = has ? bnd[rz + 5] : 0;
-        }
-        col = ncol;
-        base = nbase;
-        total = ntotal;
-    }
-    if (!has) return;
-    const double gx = (static_cast<double>(acc.hx) + static_cast<double>(acc.lx)) * bx.acc_scale;
-    const double gy = (static_cast<double>(acc.hy) + static_cast<double>(acc.ly)) * bx.acc_scale;
-    const double gz = (static_cast<double>(acc.hz) + static_cast<double>(acc.lz)) * bx.acc_scale;
-    if (bx.acc64) {
-        double *o = bx.acc64 + 3 * static_cast<int64_t>(i);
-        o[0] = gx; o[1] = gy; o[2] = gz;
-    }
-    if (bx.acc_out)
-        bx.acc_out[i] = make_float4(static_cast<float>(gx), static_cast<float>(gy), static_cast<float>(gz), 0.f);
-}
-
 // per-warp shared memory, in float4 units: staged sources (and cotangents),
-// compensated sums (3 KB; with the neighbour table, the staged lane items' cell
-// table, so reserved in plain mode too), neighbour table (256 ints), table
-// slots (2 B bytes)
+// compensated sums, neighbour table (256 ints), table slots (2 B bytes)
 template <int B, bool COMP, bool ADJ>
 __host__ __device__ constexpr int per_warp_f4()
 {
-    return (ADJ ? 4 : 2) * B + 192 + 64 + B / 8;
+    return (ADJ ? 4 : 2) * B + (COMP ? 192 : 0) + 64 + B / 8;
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -1257,7 +1054,7 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
     float4 *stage = w0;
     float4 *wstage = stage + 2 * B;
     float *comp = reinterpret_cast<float *>(w0 + (ADJ ? 4 : 2) * B);
-    int *tabs = reinterpret_cast<int *>(w0 + (ADJ ? 4 : 2) * B + 192);
+    int *tabs = reinterpret_cast<int *>(w0 + (ADJ ? 4 : 2) * B + (COMP ? 192 : 0));
     int *tstart = tabs, *tpre = tabs + 128;
     unsigned char *tslot = reinterpret_cast<unsigned char *>(tabs + 256);
     const int n_items = *n_items_p;
@@ -1278,10 +1075,7 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
         const long long t0 = prof ? clock64() : 0;
         int kind, srcs = 0;
         if (item_is_lanes(item)) {
-            if (NF_LANE_STAGED && !ADJ)
-                run_lanes_staged<B, COMP, SOFT>(bx, item, stage, reinterpret_cast<int *>(comp), tslot, lane);
-            else
-                run_lanes<COMP, ADJ, SOFT>(bx, item, lane);
+            run_lanes<COMP, ADJ, SOFT>(bx, item, lane);
             kind = 4;
         } else if (cnt <= 16) {
             srcs = run_item<0, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
