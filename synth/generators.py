@@ -311,6 +311,23 @@ def _tiles128(cpd: int = 40, per_cell: int = 128):
     return Workload(f"tiles{per_cell}", pos, cpd, (1.0 / n ** (1.0 / 3.0)) / 40.0, meta=dict(per_cell=per_cell))
 
 
+def _giantcell():
+    """One cell of 200,000 particles (the largest cell late in the paper's run holds over 200,000),
+    two dense cells (30,000 and 20,000) at Chebyshev distance 2 from it, and a sparse background of
+    4 particles per cell; CPD 12.  Each dense population is a Gaussian clipped to its cell."""
+    cpd = 12
+    rng = np.random.default_rng(81)
+    bg = rng.random((4 * cpd ** 3, 3))
+
+    def blob(cell, n, sigma):
+        c = np.asarray(cell, float)
+        x = (c + 0.5) / cpd + sigma / cpd * rng.standard_normal((n, 3))
+        return np.clip(x, c / cpd + 1e-7, (c + 1) / cpd - 1e-7)
+    pos = np.concatenate([bg, blob((3, 3, 3), 200000, 0.2), blob((5, 3, 3), 30000, 0.25),
+                          blob((3, 5, 1), 20000, 0.3)])
+    return Workload("giantcell", pos, cpd, (1.0 / 100.0) / 40.0, meta=dict(largest_cell=200000))
+
+
 def _sparse2(cpd: int = 200, per_cell: int = 2):
     """Uniform random particles at per_cell per cell on average (cpd^3 cells): almost every cell
     is sparse, so nearly all work runs as lane items (a profiling workload)."""
@@ -327,9 +344,10 @@ WORKLOADS = {
     "clustered64": _clustered64,
     "tiles128": _tiles128,
     "sparse2": _sparse2,
+    "giantcell": _giantcell,
 }
 
 
 def workload(name: str, **kw) -> Workload:
-    """Named workload: uniform32k, clustered256, zeldovich512, clustered64, tiles128, sparse2."""
+    """Named workload: uniform32k, clustered256, zeldovich512, clustered64, tiles128, sparse2, giantcell."""
     return WORKLOADS[name](**kw)

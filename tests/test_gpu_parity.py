@@ -526,17 +526,8 @@ def _giant_cell_box():
     """One cell of 200,000 particles (the largest cell late in the paper's run holds over
     200,000, Section 2.2) and two dense cells at Chebyshev distance 2 from it, in a sparse
     background (4 particles per cell)."""
-    cpd = 12
-    rng = np.random.default_rng(81)
-    bg = rng.random((4 * cpd ** 3, 3))
-
-    def blob(cell, n, sigma):
-        c = np.asarray(cell, float)
-        x = (c + 0.5) / cpd + sigma / cpd * rng.standard_normal((n, 3))
-        return np.clip(x, c / cpd + 1e-7, (c + 1) / cpd - 1e-7)
-    X = np.concatenate([bg, blob((3, 3, 3), 200000, 0.2), blob((5, 3, 3), 30000, 0.25),
-                        blob((3, 5, 1), 20000, 0.3)])
-    return X, cpd, (1.0 / 100.0) / 40.0
+    w = workload("giantcell")
+    return w.pos, w.cpd, w.eps
 
 
 def test_giant_cell_splits_across_pieces_and_cells():
