@@ -75,6 +75,9 @@ namespace {
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
+#ifndef NF_STAGE_CONTIG
+#define NF_STAGE_CONTIG 1   // each lane stages B/32 consecutive sources (one cell search per lane and round)
+#endif
 #ifndef NF_LANE_UNROLL
 #define NF_LANE_UNROLL 4   // sources per unrolled step of a lane item (independent loads in flight)
 #endif
@@ -427,6 +430,34 @@ template <int B, bool ADJ>
 __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float4 *wbuf, const int *tstart,
                                             const int *tpre, int base, int total, int lane, unsigned char *ts)
 {
+    if (NF_STAGE_CONTIG) {
+        // every lane copies B/32 consecutive entries: one search for the first, then the cell
+        // only moves forward (entries past the end become far-away padding)
+        constexpr int E = B / 32;
+        int p = -1;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int slot = lane * E + m;
+            const int f = base + slot;
+            if (f < total) {
+                if (p < 0) {
+                    p = find_cell(tpre, f);
+                } else {
+                    while (tpre[p + 1] <= f) ++p;   // tpre[125] = total > f
+                }
+                const int src = tstart[p] + (f - tpre[p]);
+                cp_async16(buf + slot, bx.pos + src);
+                if (ADJ) cp_async16(wbuf + slot, bx.cot + src);
+                ts[slot] = static_cast<unsigned char>(__ldg(&kNbrOrder.code[p]) + 1);
+            } else {
+                buf[slot] = make_float4(kFar, kFar, kFar, 0.f);
+                if (ADJ) wbuf[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+                ts[slot] = 0;
+            }
+        }
+        cp_async_commit();
+        return;
+    }
 #pragma unroll
     for (int m = 0; m < B / 32; ++m) {
         const int f = base + m * 32 + lane;
@@ -595,6 +626,9 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         } else {
             cp_async_wait_0();
         }
+        // the shift pass reads entries other lanes copied (contiguous staging): their copies are
+        // complete once each lane has passed its wait
+        if (NF_STAGE_CONTIG) __syncwarp();
         stage_shift<B, PAIRSRC>(buf, lane, tslot + (r & 1) * B);
         __syncwarp();
         const int nr = min(B, src_hi - src_lo - r * B);
