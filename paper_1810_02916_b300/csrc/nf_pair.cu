@@ -75,9 +75,6 @@ namespace {
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
-#ifndef NF_SPLIT2
-#define NF_SPLIT2 1   // tiles of 2..16 sinks hold two sinks per lane in split mode
-#endif
 #ifndef NF_STAGE_CONTIG
 #define NF_STAGE_CONTIG 1   // each lane stages B/32 consecutive sources (one cell search per lane and round)
 #endif
@@ -536,36 +533,28 @@ __device__ __forceinline__ void comp_fold_smem(float *c, float &px, float &py, f
     px = py = pz = 0.f;
 }
 
-// S = 0: split mode (<= 16 sinks), one sink per lane; S = -2: split mode, two
-// sinks per lane (2..16 sinks, forces only); S = 1, 2, 4: sinks per lane.
-// Returns the number of sources the item evaluated for each of its sinks.
+// S = 0: split mode (<= 16 sinks); S = 1, 2, 4: sinks per lane.  Returns the
+// number of sources the item evaluated for each of its sinks.
 template <int S, int B, bool COMP, bool ADJ, int SOFT>
 __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float4 *wstage, int *tstart, int *tpre,
                          float *comp, unsigned char *tslot, int lane)
 {
-    constexpr bool SPLIT = (S <= 0);
-    constexpr int SL = (S == -2) ? 2 : 1;   // sinks per lane in split mode
-    constexpr int SS = SPLIT ? SL : S;
+    constexpr bool SPLIT = (S == 0);
+    constexpr int SS = SPLIT ? 1 : S;
     const int count = item_count(item);
     int logp = 0;
     if (SPLIT) {
         while ((1 << logp) < count) ++logp;
-        if (SL == 2 && logp < 1) logp = 1;
     }
-    const int P = 1 << logp;                       // sink slots, a power of two
-    const int logpl = SPLIT ? logp - (SL == 2 ? 1 : 0) : 0;
-    const int Pl = 1 << logpl;                     // lanes per group in split mode
-    const int my_split = SPLIT ? (lane >> logpl) : 0;
-    const int splits = SPLIT ? (32 >> logpl) : 1;
-    // the sink held in register slot s, and (group 0 of split mode) the sink a lane writes
-    auto sink_of = [&](int s) { return SPLIT ? (lane & (Pl - 1)) * SL + s : lane + 32 * s; };
-    auto out_of = [&](int s) { return SPLIT ? lane * SL + s : lane + 32 * s; };
+    const int P = 1 << logp;
+    const int my_split = SPLIT ? (lane >> logp) : 0;
+    const int splits = SPLIT ? (32 >> logp) : 1;
 
     float xi[SS], yi[SS], zi[SS], wx[SS], wy[SS], wz[SS];
     float px[SS], py[SS], pz[SS];
 #pragma unroll
     for (int s = 0; s < SS; ++s) {
-        const int k = sink_of(s);
+        const int k = SPLIT ? (lane & (P - 1)) : lane + 32 * s;
         const int idx = item.sink_begin + min(k, count - 1);
         const float4 p = __ldg(bx.pos + idx);
         xi[s] = p.x; yi[s] = p.y; zi[s] = p.z;
@@ -587,9 +576,9 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
     // source (PACK); lanes with one sink pair one sink against two sources
     // (PAIRSRC: even and odd sources of a round go to the two halves of a float2
     // partial sum, both folded into the sink's sum)
-    constexpr bool PACK = NF_PACKED && !ADJ && SS >= 2 && !SPLIT;
-    constexpr bool PAIRSRC = NF_PAIR_SOURCES && !ADJ && (SS == 1 || SPLIT);
-    constexpr int SP = PACK ? SS / 2 : SS;
+    constexpr bool PACK = NF_PACKED && !ADJ && SS >= 2;
+    constexpr bool PAIRSRC = NF_PAIR_SOURCES && !ADJ && SS == 1;
+    constexpr int SP = SS >= 2 ? SS / 2 : 1;
     float2 nx2[SP], ny2[SP], nz2[SP], ax2[SP], ay2[SP], az2[SP];
     if (PACK) {
 #pragma unroll
@@ -601,13 +590,10 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         }
     }
     if (PAIRSRC) {
-#pragma unroll
-        for (int k = 0; k < SS; ++k) {
-            nx2[k] = make_float2(-xi[k], -xi[k]);
-            ny2[k] = make_float2(-yi[k], -yi[k]);
-            nz2[k] = make_float2(-zi[k], -zi[k]);
-            ax2[k] = ay2[k] = az2[k] = make_float2(0.f, 0.f);
-        }
+        nx2[0] = make_float2(-xi[0], -xi[0]);
+        ny2[0] = make_float2(-yi[0], -yi[0]);
+        nz2[0] = make_float2(-zi[0], -zi[0]);
+        ax2[0] = ay2[0] = az2[0] = make_float2(0.f, 0.f);
     }
     const float2 a02 = make_float2(a0, a0), a12 = make_float2(a1, a1), a22 = make_float2(a2, a2),
                  e22 = make_float2(eps2, eps2);
@@ -664,51 +650,34 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
             const int n_near = ((nnp + splits - 1) / splits + 1) & ~1;
             const int n_all = ((nrp + splits - 1) / splits + 1) & ~1;
             for (int i = 0; i < n_near; i += 2) {
-                const int mm[2] = {my_split + i * splits, my_split + (i + 1) * splits};
+                const int m0 = my_split + i * splits, m1 = m0 + splits;
                 if (VOTE_SPLIT) {
-                    // one vote per source pair: a pair's chains for this lane's sinks
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float2 qx = xs2[mm[h]], qy = ys2[mm[h]], qz = zs2[mm[h]];
-                        float2 dx[SS], dy[SS], dz[SS], r2[SS];
-                        float mn = 0.f;
-#pragma unroll
-                        for (int k = 0; k < SS; ++k) {
-                            dx[k] = __fadd2_rn(qx, nx2[k]);
-                            dy[k] = __fadd2_rn(qy, ny2[k]);
-                            dz[k] = __fadd2_rn(qz, nz2[k]);
-                            r2[k] = __ffma2_rn(dz[k], dz[k], __ffma2_rn(dy[k], dy[k],
-                                               __ffma2_rn(dx[k], dx[k], make_float2(FLT_MIN, FLT_MIN))));
-                            const float m2 = fminf(r2[k].x, r2[k].y);
-                            mn = k == 0 ? m2 : fminf(mn, m2);
-                        }
-                        if (__any_sync(kFull, mn < eps2)) {
-#pragma unroll
-                            for (int k = 0; k < SS; ++k)
-                                tail2_spline(dx[k], dy[k], dz[k], r2[k], ax2[k], ay2[k], az2[k], a02, a12, a22);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < SS; ++k) tail2_newton(dx[k], dy[k], dz[k], r2[k], ax2[k], ay2[k], az2[k]);
-                        }
+                    const float2 dx0 = __fadd2_rn(xs2[m0], nx2[0]), dy0 = __fadd2_rn(ys2[m0], ny2[0]),
+                                 dz0 = __fadd2_rn(zs2[m0], nz2[0]);
+                    const float2 dx1 = __fadd2_rn(xs2[m1], nx2[0]), dy1 = __fadd2_rn(ys2[m1], ny2[0]),
+                                 dz1 = __fadd2_rn(zs2[m1], nz2[0]);
+                    const float2 fm = make_float2(FLT_MIN, FLT_MIN);
+                    const float2 r20 = __ffma2_rn(dz0, dz0, __ffma2_rn(dy0, dy0, __ffma2_rn(dx0, dx0, fm)));
+                    const float2 r21 = __ffma2_rn(dz1, dz1, __ffma2_rn(dy1, dy1, __ffma2_rn(dx1, dx1, fm)));
+                    if (__any_sync(kFull, fminf(fminf(r20.x, r20.y), fminf(r21.x, r21.y)) < eps2)) {
+                        tail2_spline(dx0, dy0, dz0, r20, ax2[0], ay2[0], az2[0], a02, a12, a22);
+                        tail2_spline(dx1, dy1, dz1, r21, ax2[0], ay2[0], az2[0], a02, a12, a22);
+                    } else {
+                        tail2_newton(dx0, dy0, dz0, r20, ax2[0], ay2[0], az2[0]);
+                        tail2_newton(dx1, dy1, dz1, r21, ax2[0], ay2[0], az2[0]);
                     }
                 } else {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)
-#pragma unroll
-                        for (int k = 0; k < SS; ++k)
-                            pair_force2<SOFT>(xs2[mm[h]], ys2[mm[h]], zs2[mm[h]], nx2[k], ny2[k], nz2[k], ax2[k],
-                                              ay2[k], az2[k], a02, a12, a22, e22);
+                    pair_force2<SOFT>(xs2[m0], ys2[m0], zs2[m0], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0],
+                                      a02, a12, a22, e22);
+                    pair_force2<SOFT>(xs2[m1], ys2[m1], zs2[m1], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0],
+                                      a02, a12, a22, e22);
                 }
             }
             if (FARSPLIT)
                 for (int i = n_near; i < n_all; i += 2) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int m = my_split + (i + h) * splits;
-#pragma unroll
-                        for (int k = 0; k < SS; ++k)
-                            pair_force2_far(xs2[m], ys2[m], zs2[m], nx2[k], ny2[k], nz2[k], ax2[k], ay2[k], az2[k]);
-                    }
+                    const int m0 = my_split + i * splits, m1 = m0 + splits;
+                    pair_force2_far(xs2[m0], ys2[m0], zs2[m0], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0]);
+                    pair_force2_far(xs2[m1], ys2[m1], zs2[m1], nx2[0], ny2[0], nz2[0], ax2[0], ay2[0], az2[0]);
                 }
         } else if (PAIRSRC) {
             constexpr int U2 = NF_PAIR_UNROLL;
@@ -843,11 +812,8 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         }
         if (COMP) {
             if (PAIRSRC) {
-#pragma unroll
-                for (int k = 0; k < SS; ++k) {
-                    comp_fold_smem(comp + lane + 32 * k, ax2[k].x, ay2[k].x, az2[k].x);
-                    comp_fold_smem(comp + lane + 32 * k, ax2[k].y, ay2[k].y, az2[k].y);
-                }
+                comp_fold_smem(comp + lane, ax2[0].x, ay2[0].x, az2[0].x);
+                comp_fold_smem(comp + lane, ax2[0].y, ay2[0].y, az2[0].y);
             } else if (PACK) {
 #pragma unroll
                 for (int k = 0; k < SP; ++k) {
@@ -862,12 +828,9 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         __syncwarp();
     }
     if (PAIRSRC && !COMP) {
-#pragma unroll
-        for (int k = 0; k < SS; ++k) {
-            px[k] = ax2[k].x + ax2[k].y;
-            py[k] = ay2[k].x + ay2[k].y;
-            pz[k] = az2[k].x + az2[k].y;
-        }
+        px[0] = ax2[0].x + ax2[0].y;
+        py[0] = ay2[0].x + ay2[0].y;
+        pz[0] = az2[0].x + az2[0].y;
     }
     if (PACK && !COMP) {
 #pragma unroll
@@ -882,7 +845,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         float sxp[SS], syp[SS], szp[SS], mx[SS], my[SS], mz[SS];
 #pragma unroll
         for (int s = 0; s < SS; ++s) {
-            const int k = sink_of(s);
+            const int k = SPLIT ? (lane & (P - 1)) : lane + 32 * s;
             const float4 p = __ldg(bx.pos + item.sink_begin + min(k, count - 1));
             sxp[s] = p.x; syp[s] = p.y; szp[s] = p.z;
             mx[s] = my[s] = mz[s] = 0.f;
@@ -936,16 +899,13 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         }
     }
     if (SPLIT) {
-        for (int o = Pl; o < 32; o <<= 1) {
-#pragma unroll
-            for (int s = 0; s < SS; ++s) {
-                if (COMP) {
-                    comp_xor_combine(acc[s], o);
-                } else {
-                    acc[s].hx += __shfl_xor_sync(kFull, acc[s].hx, o);
-                    acc[s].hy += __shfl_xor_sync(kFull, acc[s].hy, o);
-                    acc[s].hz += __shfl_xor_sync(kFull, acc[s].hz, o);
-                }
+        for (int o = P; o < 32; o <<= 1) {
+            if (COMP) {
+                comp_xor_combine(acc[0], o);
+            } else {
+                acc[0].hx += __shfl_xor_sync(kFull, acc[0].hx, o);
+                acc[0].hy += __shfl_xor_sync(kFull, acc[0].hy, o);
+                acc[0].hz += __shfl_xor_sync(kFull, acc[0].hz, o);
             }
         }
     }
@@ -954,7 +914,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         const int slot = __ldg(&bx.pieces[item.piece].slot);
 #pragma unroll
         for (int s = 0; s < SS; ++s) {
-            const int k = out_of(s);
+            const int k = SPLIT ? lane : lane + 32 * s;
             if (k < count) {
                 double *o = bx.partials + 3 * (static_cast<int64_t>(slot) + k);
                 o[0] = static_cast<double>(acc[s].hx) + static_cast<double>(acc[s].lx);
@@ -967,7 +927,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
     const double scale = ADJ ? bx.grad_scale : bx.acc_scale;
 #pragma unroll
     for (int s = 0; s < SS; ++s) {
-        const int k = out_of(s);
+        const int k = SPLIT ? lane : lane + 32 * s;
         if (k < count) {
             const int idx = item.sink_begin + k;
             const double gx = (static_cast<double>(acc[s].hx) + static_cast<double>(acc[s].lx)) * scale;
@@ -1152,14 +1112,7 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
             run_lanes<COMP, ADJ, SOFT>(bx, item, lane);
             kind = 4;
         } else if (cnt <= 16) {
-            bool two = false;
-            if constexpr (NF_SPLIT2 && !ADJ) {
-                if (cnt >= 2) {
-                    srcs = run_item<-2, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
-                    two = true;
-                }
-            }
-            if (!two) srcs = run_item<0, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            srcs = run_item<0, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
             kind = 3;
         } else if (cnt <= 32) {
             srcs = run_item<1, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
