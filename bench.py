@@ -402,6 +402,7 @@ def run_forces_only(args):
         nf.set_accumulation(nfb.ACC_PLAIN)
     nf.bin_particles(torch.from_numpy(w.pos).cuda())
     acc = torch.empty((nf.n, 4), dtype=torch.float32, device="cuda")
+    nf.forces(acc)                      # untimed first pass (one-time kernel set-up)
     nf.profile(2 if args.class_profile else True)
     for _ in range(args.forces_only):
         nf.forces(acc)

@@ -75,6 +75,12 @@ namespace {
 #ifndef NF_MIN_BLOCKS
 #define NF_MIN_BLOCKS 3   // resident 256-thread blocks per SM the register budget must allow
 #endif
+#ifndef NF_ADJ_UNROLL
+#define NF_ADJ_UNROLL 4   // staged sources per unrolled step of the adjoint
+#endif
+#ifndef NF_PACKED_ADJ
+#define NF_PACKED_ADJ 1   // the adjoint evaluates two sinks per paired FP32 instruction on 2- and 4-sink lanes
+#endif
 #ifndef NF_STAGE_CONTIG
 #define NF_STAGE_CONTIG 1   // each lane stages B/32 consecutive sources (one cell search per lane and round)
 #endif
@@ -313,9 +319,9 @@ __device__ __forceinline__ void pair_adjoint(const float4 q, const float4 wj, fl
         f = y2 * y;
         hh = -3.f * f * y2;
     } else {
-        float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        // + FLT_MIN as in the forces: it changes nothing but r = 0, where it keeps rsqrt finite
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, FLT_MIN)));
         const bool inside = r2 < eps2;
-        r2 = fmaxf(r2, FLT_MIN);
         float y = rsqrtf(r2);
         const float t = r2 * y;
         const float h = t * y;
@@ -334,6 +340,56 @@ __device__ __forceinline__ void pair_adjoint(const float4 q, const float4 wj, fl
     gx = fmaf(hd, dx, fmaf(f, ux, gx));
     gy = fmaf(hd, dy, fmaf(f, uy, gy));
     gz = fmaf(hd, dz, fmaf(f, uz, gz));
+}
+
+// pair_adjoint for two sinks against one source with paired FP32 instructions: every
+// lane of a pair follows the scalar arithmetic (same roundings, same order), so results
+// are bit-identical.  nx, ny, nz and nwx, nwy, nwz hold minus the sinks'
+// offsets and cotangents; a2x2 = 2 a2.
+template <int SOFT>
+__device__ __forceinline__ void pair_adjoint2(const float2 qx, const float2 qy, const float2 qz, const float2 wjx,
+                                              const float2 wjy, const float2 wjz, const float2 nx, const float2 ny,
+                                              const float2 nz, const float2 nwx, const float2 nwy, const float2 nwz,
+                                              float2 &gx, float2 &gy, float2 &gz, const float2 a0, const float2 a1,
+                                              const float2 a2, const float2 a2x2, float eps2)
+{
+    const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
+    const float2 half = make_float2(0.5f, 0.5f), mhalf = make_float2(-0.5f, -0.5f);
+    float2 f, hh;
+    if (SOFT == 1) {
+        const float2 e2 = make_float2(eps2, eps2);
+        const float2 s2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e2)));
+        float2 y = make_float2(rsqrtf(s2.x), rsqrtf(s2.y));
+        const float2 t = __fmul2_rn(s2, y);
+        const float2 h = __fmul2_rn(t, y);
+        const float2 e = __ffma2_rn(h, mhalf, half);
+        y = __ffma2_rn(y, e, y);
+        const float2 y2 = __fmul2_rn(y, y);
+        f = __fmul2_rn(y2, y);
+        hh = __fmul2_rn(__fmul2_rn(make_float2(-3.f, -3.f), f), y2);
+    } else {
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(FLT_MIN, FLT_MIN))));
+        const bool in_x = r2.x < eps2, in_y = r2.y < eps2;
+        float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        const float2 t = __fmul2_rn(r2, y);
+        const float2 h = __fmul2_rn(t, y);
+        const float2 e = __ffma2_rn(h, mhalf, half);
+        y = __ffma2_rn(y, e, y);
+        const float2 r = __ffma2_rn(t, e, t);
+        const float2 y2 = __fmul2_rn(y, y);
+        const float2 y3 = __fmul2_rn(y2, y);
+        const float2 poly = __ffma2_rn(__ffma2_rn(a2, r, a1), r, a0);
+        const float2 hin = __ffma2_rn(a1, y, a2x2);
+        const float2 hout = __fmul2_rn(__fmul2_rn(make_float2(-3.f, -3.f), y3), y2);
+        f = make_float2(in_x ? poly.x : y3.x, in_y ? poly.y : y3.y);
+        hh = make_float2(in_x ? hin.x : hout.x, in_y ? hin.y : hout.y);
+    }
+    const float2 ux = __fadd2_rn(wjx, nwx), uy = __fadd2_rn(wjy, nwy), uz = __fadd2_rn(wjz, nwz);
+    const float2 du = __ffma2_rn(dz, uz, __ffma2_rn(dy, uy, __fmul2_rn(dx, ux)));
+    const float2 hd = __fmul2_rn(hh, du);
+    gx = __ffma2_rn(hd, dx, __ffma2_rn(f, ux, gx));
+    gy = __ffma2_rn(hd, dy, __ffma2_rn(f, uy, gy));
+    gz = __ffma2_rn(hd, dz, __ffma2_rn(f, uz, gz));
 }
 
 // Order of the neighbour table: the 27 cells within one cell of the sink cell
@@ -577,10 +633,20 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
     // (PAIRSRC: even and odd sources of a round go to the two halves of a float2
     // partial sum, both folded into the sink's sum)
     constexpr bool PACK = NF_PACKED && !ADJ && SS >= 2;
+    constexpr bool PACKA = NF_PACKED_ADJ && ADJ && SS >= 2;   // the adjoint, two sinks per paired instruction
     constexpr bool PAIRSRC = NF_PAIR_SOURCES && !ADJ && SS == 1;
     constexpr int SP = SS >= 2 ? SS / 2 : 1;
     float2 nx2[SP], ny2[SP], nz2[SP], ax2[SP], ay2[SP], az2[SP];
-    if (PACK) {
+    float2 nwx2[SP], nwy2[SP], nwz2[SP];
+    if (PACKA) {
+#pragma unroll
+        for (int k = 0; k < SP; ++k) {
+            nwx2[k] = make_float2(-wx[2 * k], -wx[2 * k + 1]);
+            nwy2[k] = make_float2(-wy[2 * k], -wy[2 * k + 1]);
+            nwz2[k] = make_float2(-wz[2 * k], -wz[2 * k + 1]);
+        }
+    }
+    if (PACK || PACKA) {
 #pragma unroll
         for (int k = 0; k < SP; ++k) {
             nx2[k] = make_float2(-xi[2 * k], -xi[2 * k + 1]);
@@ -721,7 +787,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
             if (FARSPLIT && !ADJ)
                 for (; j < nr; j += splits) pair_force_far(buf[j], xi[0], yi[0], zi[0], px[0], py[0], pz[0]);
         } else {
-            constexpr int U = SS == 2 ? NF_UNROLL_S2 : NF_SRC_UNROLL;
+            constexpr int U = ADJ ? NF_ADJ_UNROLL : SS == 2 ? NF_UNROLL_S2 : NF_SRC_UNROLL;
             // padding entries add exact zeros under either law; the near loop's last
             // step may take up to U - 1 far entries, which the full law treats exactly
             const int nru = (nr + U - 1) / U * U;
@@ -779,6 +845,17 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
                         for (int k = 0; k < SP; ++k)
                             pair_force2<SOFT>(qx, qy, qz, nx2[k], ny2[k], nz2[k], ax2[k], ay2[k], az2[k], a02, a12,
                                               a22, e22);
+                    } else if (PACKA) {
+                        const float4 wq = wbuf[j + u];
+                        const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
+                                     qz = make_float2(q.z, q.z);
+                        const float2 wjx = make_float2(wq.x, wq.x), wjy = make_float2(wq.y, wq.y),
+                                     wjz = make_float2(wq.z, wq.z);
+                        const float2 a2x2 = make_float2(2.f * a2, 2.f * a2);
+#pragma unroll
+                        for (int k = 0; k < SP; ++k)
+                            pair_adjoint2<SOFT>(qx, qy, qz, wjx, wjy, wjz, nx2[k], ny2[k], nz2[k], nwx2[k], nwy2[k],
+                                                nwz2[k], ax2[k], ay2[k], az2[k], a02, a12, a22, a2x2, eps2);
                     } else if (ADJ) {
                         const float4 wq = wbuf[j + u];
 #pragma unroll
@@ -814,7 +891,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
             if (PAIRSRC) {
                 comp_fold_smem(comp + lane, ax2[0].x, ay2[0].x, az2[0].x);
                 comp_fold_smem(comp + lane, ax2[0].y, ay2[0].y, az2[0].y);
-            } else if (PACK) {
+            } else if (PACK || PACKA) {
 #pragma unroll
                 for (int k = 0; k < SP; ++k) {
                     comp_fold_smem(comp + lane + 32 * (2 * k), ax2[k].x, ay2[k].x, az2[k].x);
@@ -832,7 +909,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         py[0] = ay2[0].x + ay2[0].y;
         pz[0] = az2[0].x + az2[0].y;
     }
-    if (PACK && !COMP) {
+    if ((PACK || PACKA) && !COMP) {
 #pragma unroll
         for (int k = 0; k < SP; ++k) {
             px[2 * k] = ax2[k].x; py[2 * k] = ay2[k].x; pz[2 * k] = az2[k].x;
