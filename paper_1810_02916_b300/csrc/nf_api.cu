@@ -57,7 +57,8 @@ struct nf_box {
     uint32_t *keys[2] = {nullptr, nullptr}, *vals[2] = {nullptr, nullptr};
     int cur = 0;                      // keys[cur] = cell of each stored particle, vals[cur] = its id
     // per-id scratch used by binning and re-binning
-    float4 *xq_by_id = nullptr, *vel_by_id = nullptr;
+    float4 *xq_by_id = nullptr;       // binned offsets by id (loads)
+    float4 *state_by_id = nullptr;    // 2 float4 per id: drifted offset (key bits in w), velocity
     // cells
     int *cell_start = nullptr, *counts = nullptr, *offsets = nullptr;
     void *scan_tmp = nullptr, *radix_tmp = nullptr;
@@ -215,7 +216,7 @@ void free_particles(nf_t *nf)
 {
     dfree(nf->pos); dfree(nf->vel); dfree(nf->acc64); dfree(nf->acc32); dfree(nf->cot);
     for (int k = 0; k < 2; ++k) { dfree(nf->keys[k]); dfree(nf->vals[k]); }
-    dfree(nf->xq_by_id); dfree(nf->vel_by_id);
+    dfree(nf->xq_by_id); dfree(nf->state_by_id);
     dfree(nf->items); dfree(nf->items_raw); dfree(nf->pieces); dfree(nf->reduces); dfree(nf->partials);
     dfree(nf->split_k); dfree(nf->split_p); dfree(nf->split_r);
     if (nf->split_scan) cudaFree(nf->split_scan);
@@ -251,7 +252,7 @@ int ensure_capacity(nf_t *nf, int64_t n)
         (rc = dalloc(nf, &nf->acc64, 3 * sizeof(double) * static_cast<size_t>(c))) ||
         (rc = dalloc(nf, &nf->keys[0], u4)) || (rc = dalloc(nf, &nf->keys[1], u4)) ||
         (rc = dalloc(nf, &nf->vals[0], u4)) || (rc = dalloc(nf, &nf->vals[1], u4)) ||
-        (rc = dalloc(nf, &nf->xq_by_id, f4)) || (rc = dalloc(nf, &nf->vel_by_id, f4))) {
+        (rc = dalloc(nf, &nf->xq_by_id, f4)) || (rc = dalloc(nf, &nf->state_by_id, 2 * f4))) {
         free_particles(nf);
         return rc;
     }
@@ -401,8 +402,12 @@ int sort_and_gather(nf_t *nf, int src, bool with_vel)
     NF_CK(nf::radix_sort_pairs(nf->keys[src], nf->vals[src], nf->keys[1 - src], nf->vals[1 - src], nf->n,
                                key_bits(nf->ncell), nf->radix_tmp, &in_alt, nf->stream));
     nf->cur = in_alt ? 1 - src : src;
-    NF_CK(nf::gather_sorted(nf->vals[nf->cur], nf->xq_by_id, with_vel ? nf->vel_by_id : nullptr, nf->pos, nf->vel,
-                            static_cast<int>(nf->n), nf->stream));
+    if (with_vel)
+        NF_CK(nf::gather_state(nf->vals[nf->cur], nf->state_by_id, nf->pos, nf->vel, static_cast<int>(nf->n),
+                               nf->stream));
+    else
+        NF_CK(nf::gather_sorted(nf->vals[nf->cur], nf->xq_by_id, nullptr, nf->pos, nf->vel, static_cast<int>(nf->n),
+                                nf->stream));
     return NF_OK;
 }
 
@@ -933,16 +938,16 @@ int nf_kick_drift(nf_t *nf, double dt)
     const int n = static_cast<int>(nf->n);
     if (n == 0) return NF_OK;
     NF_CK(cudaMemsetAsync(nf->err, 0, sizeof(int), nf->stream));
-    // the new state goes to scratch (xq_by_id, vel_by_id), so a refused step changes nothing
+    // the new state goes to scratch (state_by_id), so a refused step changes nothing
     NF_CK(nf::kick_drift(nf->pos, nf->vel, nf->acc64, nf->keys[nf->cur], nf->vals[nf->cur], dt, nf->inv_w, nf->cpd,
-                         n, nf->xq_by_id, nf->vel_by_id, nf->err, nf->stream));
+                         n, nf->state_by_id, nf->err, nf->stream));
     int viol = 0;
     if ((rc = read_err(nf, &viol))) return rc;
     if (viol)
         return fail(nf, NF_EINVAL, std::to_string(viol) + " particles would drift more than 0.8 cell widths");
     const int src = 1 - nf->cur;
     NF_CK(cudaMemsetAsync(nf->counts, 0, sizeof(int) * (static_cast<size_t>(nf->ncell) + 2), nf->stream));
-    NF_CK(nf::drift_keys(nf->xq_by_id, n, nf->keys[src], nf->vals[src], nf->counts, nf->stream));
+    NF_CK(nf::drift_keys(nf->state_by_id, n, nf->keys[src], nf->vals[src], nf->counts, nf->stream));
     if ((rc = sort_and_gather(nf, src, true))) return rc;
     if ((rc = counts_to_cell_start(nf))) return rc;
     if ((rc = plan(nf))) return rc;

@@ -21,8 +21,7 @@ inline int nblocks(int64_t n, int per) { return static_cast<int>((n + per - 1) /
 __global__ void kick_drift_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
                                   const double *__restrict__ acc64, const uint32_t *__restrict__ cell_of,
                                   const uint32_t *__restrict__ perm, double dt, double inv_w, int cpd, int n,
-                                  float4 *__restrict__ xq_by_id, float4 *__restrict__ vel_by_id,
-                                  int *__restrict__ violations)
+                                  float4 *__restrict__ state_by_id, int *__restrict__ violations)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -50,16 +49,19 @@ __global__ void kick_drift_kernel(const float4 *__restrict__ pos, const float4 *
     bin_cell_units(sz, cpd, nz, qz);
     const uint32_t id = perm[k];
     const uint32_t key = static_cast<uint32_t>((nx * cpd + ny) * cpd + nz);
-    xq_by_id[id] = make_float4(qx, qy, qz, __uint_as_float(key));   // key bits: moved, never computed with
-    vel_by_id[id] = make_float4(vx, vy, vz, 0.f);
+    // one 32-byte record per particle (offset with the key bits, then the velocity), written by
+    // two adjacent 16-byte stores: the scattered writes fill whole 32-byte sectors
+    float4 *rec = state_by_id + 2 * static_cast<int64_t>(id);
+    rec[0] = make_float4(qx, qy, qz, __uint_as_float(key));   // key bits: moved, never computed with
+    rec[1] = make_float4(vx, vy, vz, 0.f);
 }
 
-__global__ void keys_from_state(const float4 *__restrict__ xq_by_id, int n, uint32_t *__restrict__ keys,
+__global__ void keys_from_state(const float4 *__restrict__ state_by_id, int n, uint32_t *__restrict__ keys,
                                 uint32_t *__restrict__ vals, int *__restrict__ counts)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const uint32_t key = __float_as_uint(xq_by_id[k].w);
+    const uint32_t key = __float_as_uint(state_by_id[2 * static_cast<int64_t>(k)].w);
     keys[k] = key;
     vals[k] = static_cast<uint32_t>(k);
     atomicAdd(&counts[key], 1);
@@ -68,19 +70,19 @@ __global__ void keys_from_state(const float4 *__restrict__ xq_by_id, int n, uint
 }  // namespace
 
 cudaError_t kick_drift(const float4 *pos, const float4 *vel, const double *acc64, const uint32_t *cell_of,
-                       const uint32_t *perm, double dt, double inv_w, int cpd, int n, float4 *xq_by_id,
-                       float4 *vel_by_id, int *cap_violations, cudaStream_t st)
+                       const uint32_t *perm, double dt, double inv_w, int cpd, int n, float4 *state_by_id,
+                       int *cap_violations, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    kick_drift_kernel<<<nblocks(n, 256), 256, 0, st>>>(pos, vel, acc64, cell_of, perm, dt, inv_w, cpd, n, xq_by_id,
-                                                       vel_by_id, cap_violations);
+    kick_drift_kernel<<<nblocks(n, 256), 256, 0, st>>>(pos, vel, acc64, cell_of, perm, dt, inv_w, cpd, n,
+                                                       state_by_id, cap_violations);
     return cudaGetLastError();
 }
 
-cudaError_t drift_keys(const float4 *xq_by_id, int n, uint32_t *keys, uint32_t *vals, int *counts, cudaStream_t st)
+cudaError_t drift_keys(const float4 *state_by_id, int n, uint32_t *keys, uint32_t *vals, int *counts, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    keys_from_state<<<nblocks(n, 256), 256, 0, st>>>(xq_by_id, n, keys, vals, counts);
+    keys_from_state<<<nblocks(n, 256), 256, 0, st>>>(state_by_id, n, keys, vals, counts);
     return cudaGetLastError();
 }
 
