@@ -125,16 +125,43 @@ __global__ void radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shi
 }
 
 // Stable scatter: within a tile, elements are ranked in order (round by
-// round, warp by warp, lane by lane) among elements of the same digit.
+// round, warp by warp, lane by lane) among elements of the same digit.  The
+// tile is first laid out in shared memory in output order (digit by digit),
+// then written so that consecutive threads write consecutive elements of each
+// digit's run: the global writes come in runs rather than one element per
+// digit and round.
 __global__ void radix_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
-                              int shift, int nb, const int *__restrict__ offs, uint32_t *__restrict__ keys_out,
-                              uint32_t *__restrict__ vals_out)
+                              int shift, int nb, const int *__restrict__ hist, const int *__restrict__ offs,
+                              uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out)
 {
-    __shared__ int run[256];
+    __shared__ int run[256];                      // running local position of each digit
+    __shared__ int lstart[256];                   // the digit's first local position
+    __shared__ int gbase[256];                    // the digit's first global position for this tile
+    __shared__ int wtot[kRsThreads / 32];
     __shared__ int wcnt[kRsThreads / 32][256];
+    __shared__ uint32_t skey[kRsTile], sval[kRsTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    run[threadIdx.x] = offs[static_cast<int64_t>(threadIdx.x) * nb + blockIdx.x];
     const int64_t tile = static_cast<int64_t>(blockIdx.x) * kRsTile;
+    const int count = static_cast<int>(n - tile < kRsTile ? n - tile : kRsTile);
+    {
+        // the tile's digit counts (histogram pass) -> local starts by a block scan
+        const int d = threadIdx.x;
+        const int c = hist[static_cast<int64_t>(d) * nb + blockIdx.x];
+        gbase[d] = offs[static_cast<int64_t>(d) * nb + blockIdx.x];
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wtot[warp] = x;
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += wtot[w];
+        lstart[d] = before + x - c;
+        run[d] = before + x - c;
+    }
+    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
     for (int r = 0; r < kRsRounds; ++r) {
 #pragma unroll
@@ -161,11 +188,19 @@ __global__ void radix_scatter(const uint32_t *__restrict__ keys, const uint32_t 
         }
         __syncthreads();
         if (valid) {
-            const int dest = wcnt[warp][d] + rank;
-            keys_out[dest] = key;
-            vals_out[dest] = val;
+            const int lpos = wcnt[warp][d] + rank;   // output order within the tile
+            skey[lpos] = key;
+            sval[lpos] = val;
         }
         __syncthreads();
+    }
+    // write out in output order: element j of the tile goes to its digit's global run
+    for (int j = threadIdx.x; j < count; j += kRsThreads) {
+        const uint32_t key = skey[j];
+        const int d = static_cast<int>((key >> shift) & 255u);
+        const int dest = gbase[d] + (j - lstart[d]);
+        keys_out[dest] = key;
+        vals_out[dest] = sval[j];
     }
 }
 
@@ -314,7 +349,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
         radix_hist<<<nb, kRsThreads, 0, st>>>(ki, n, 8 * p, nb, hist);
         cudaError_t e = exclusive_scan_i32(hist, offs, hist_n, scan_tmp, st);
         if (e != cudaSuccess) return e;
-        radix_scatter<<<nb, kRsThreads, 0, st>>>(ki, vi, n, 8 * p, nb, offs, ko, vo);
+        radix_scatter<<<nb, kRsThreads, 0, st>>>(ki, vi, n, 8 * p, nb, hist, offs, ko, vo);
         uint32_t *t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
     }
