@@ -58,8 +58,7 @@ struct nf_box {
     int cur = 0;                      // keys[cur] = cell of each stored particle, vals[cur] = its id
     // per-id scratch used by binning and re-binning
     float4 *xq_by_id = nullptr;       // binned offsets by id (loads)
-    float4 *rec = nullptr;            // re-binning: 2 float4 per particle (drifted offset, velocity)
-    uint32_t *aux = nullptr;          // re-binning: new cell per storage index, then sort scratch
+    float4 *state_by_id = nullptr;    // 2 float4 per id: drifted offset (key bits in w), velocity
     // cells
     int *cell_start = nullptr, *counts = nullptr, *offsets = nullptr;
     void *scan_tmp = nullptr, *radix_tmp = nullptr;
@@ -217,7 +216,7 @@ void free_particles(nf_t *nf)
 {
     dfree(nf->pos); dfree(nf->vel); dfree(nf->acc64); dfree(nf->acc32); dfree(nf->cot);
     for (int k = 0; k < 2; ++k) { dfree(nf->keys[k]); dfree(nf->vals[k]); }
-    dfree(nf->xq_by_id); dfree(nf->rec); dfree(nf->aux);
+    dfree(nf->xq_by_id); dfree(nf->state_by_id);
     dfree(nf->items); dfree(nf->items_raw); dfree(nf->pieces); dfree(nf->reduces); dfree(nf->partials);
     dfree(nf->split_k); dfree(nf->split_p); dfree(nf->split_r);
     if (nf->split_scan) cudaFree(nf->split_scan);
@@ -253,8 +252,7 @@ int ensure_capacity(nf_t *nf, int64_t n)
         (rc = dalloc(nf, &nf->acc64, 3 * sizeof(double) * static_cast<size_t>(c))) ||
         (rc = dalloc(nf, &nf->keys[0], u4)) || (rc = dalloc(nf, &nf->keys[1], u4)) ||
         (rc = dalloc(nf, &nf->vals[0], u4)) || (rc = dalloc(nf, &nf->vals[1], u4)) ||
-        (rc = dalloc(nf, &nf->xq_by_id, f4)) || (rc = dalloc(nf, &nf->rec, 2 * f4)) ||
-        (rc = dalloc(nf, &nf->aux, u4))) {
+        (rc = dalloc(nf, &nf->xq_by_id, f4)) || (rc = dalloc(nf, &nf->state_by_id, 2 * f4))) {
         free_particles(nf);
         return rc;
     }
@@ -397,15 +395,19 @@ int counts_to_cell_start(nf_t *nf)
     return NF_OK;
 }
 
-// sort (keys[src], vals[src]) by key; gather positions (velocities: zero)
-int sort_and_gather(nf_t *nf, int src)
+// sort (keys[src], vals[src]) by key; gather positions (and velocities)
+int sort_and_gather(nf_t *nf, int src, bool with_vel)
 {
     int in_alt = 0;
     NF_CK(nf::radix_sort_pairs(nf->keys[src], nf->vals[src], nf->keys[1 - src], nf->vals[1 - src], nf->n,
                                key_bits(nf->ncell), nf->radix_tmp, &in_alt, nf->stream));
     nf->cur = in_alt ? 1 - src : src;
-    NF_CK(nf::gather_sorted(nf->vals[nf->cur], nf->xq_by_id, nullptr, nf->pos, nf->vel, static_cast<int>(nf->n),
-                            nf->stream));
+    if (with_vel)
+        NF_CK(nf::gather_state(nf->vals[nf->cur], nf->state_by_id, nf->pos, nf->vel, static_cast<int>(nf->n),
+                               nf->stream));
+    else
+        NF_CK(nf::gather_sorted(nf->vals[nf->cur], nf->xq_by_id, nullptr, nf->pos, nf->vel, static_cast<int>(nf->n),
+                                nf->stream));
     return NF_OK;
 }
 
@@ -707,7 +709,7 @@ int nf_bin_particles(nf_t *nf, const double *xyz, int64_t n)
     nf->have_particles = false;
     nf->have_forces = false;
     if (n > 0) {
-        if ((rc = sort_and_gather(nf, src))) return rc;
+        if ((rc = sort_and_gather(nf, src, false))) return rc;
     }
     if ((rc = counts_to_cell_start(nf))) return rc;
     NF_CK(cudaMemsetAsync(nf->vel, 0, sizeof(float4) * static_cast<size_t>(n < 1 ? 1 : n), nf->stream));
@@ -936,35 +938,17 @@ int nf_kick_drift(nf_t *nf, double dt)
     const int n = static_cast<int>(nf->n);
     if (n == 0) return NF_OK;
     NF_CK(cudaMemsetAsync(nf->err, 0, sizeof(int), nf->stream));
-    // the new state goes to scratch (rec, keys/vals[src], aux), so a refused step changes nothing
-    const int src = 1 - nf->cur;
+    // the new state goes to scratch (state_by_id), so a refused step changes nothing
     NF_CK(nf::kick_drift(nf->pos, nf->vel, nf->acc64, nf->keys[nf->cur], nf->vals[nf->cur], dt, nf->inv_w, nf->cpd,
-                         n, nf->rec, nf->keys[src], nf->vals[src], nf->aux, nf->err, nf->stream));
+                         n, nf->state_by_id, nf->err, nf->stream));
     int viol = 0;
     if ((rc = read_err(nf, &viol))) return rc;
     if (viol)
         return fail(nf, NF_EINVAL, std::to_string(viol) + " particles would drift more than 0.8 cell widths");
-    // re-binning without scattered writes: (id, storage index) sorted by id gives each id's
-    // storage index; the new cells in id order, sorted stably by cell, give the new order
-    // (cells in id order within, as a fresh binning); the records are then gathered
-    int alt1 = 0, alt2 = 0;
-    NF_CK(nf::radix_sort_pairs(nf->keys[src], nf->vals[src], nf->keys[nf->cur], nf->vals[nf->cur], n,
-                               key_bits(n), nf->radix_tmp, &alt1, nf->stream));
-    const int r1 = alt1 ? nf->cur : src;      // vals[r1][id] = storage index of id
-    const int other = 1 - r1;
+    const int src = 1 - nf->cur;
     NF_CK(cudaMemsetAsync(nf->counts, 0, sizeof(int) * (static_cast<size_t>(nf->ncell) + 2), nf->stream));
-    NF_CK(nf::drift_cell_keys(nf->vals[r1], nf->aux, n, nf->keys[other], nf->vals[other], nf->counts, nf->stream));
-    NF_CK(nf::radix_sort_pairs(nf->keys[other], nf->vals[other], nf->keys[r1], nf->aux, n, key_bits(nf->ncell),
-                               nf->radix_tmp, &alt2, nf->stream));
-    if (!alt2) {
-        NF_CK(nf::drift_gather(nf->vals[other], nf->vals[r1], nf->rec, nf->pos, nf->vel, n, nf->stream));
-        nf->cur = other;
-    } else {
-        // the sorted (cells, ids) sit in (keys[r1], aux): gather, then aux becomes vals[r1]
-        NF_CK(nf::drift_gather(nf->aux, nf->vals[r1], nf->rec, nf->pos, nf->vel, n, nf->stream));
-        std::swap(nf->aux, nf->vals[r1]);
-        nf->cur = r1;
-    }
+    NF_CK(nf::drift_keys(nf->state_by_id, n, nf->keys[src], nf->vals[src], nf->counts, nf->stream));
+    if ((rc = sort_and_gather(nf, src, true))) return rc;
     if ((rc = counts_to_cell_start(nf))) return rc;
     if ((rc = plan(nf))) return rc;
     nf->box_dirty = true;

@@ -165,6 +165,9 @@ cudaError_t gather_sorted(const uint32_t *perm, const float4 *xq_by_id, const fl
                           float4 *vel, int n, cudaStream_t st);
 cudaError_t validate_loaded(const int64_t *offsets, const int32_t *counts, const float4 *pos, int ncell, int n,
                             int *cell_start, float4 *pos_out, int *err, cudaStream_t st);
+// storage order from the drift's per-id records (state_by_id: 2 float4 per id)
+cudaError_t gather_state(const uint32_t *perm, const float4 *state_by_id, float4 *pos, float4 *vel, int n,
+                         cudaStream_t st);
 cudaError_t fill_cell_ids(const int *cell_start, int ncell, int n, uint32_t *cell_of, cudaStream_t st);
 cudaError_t iota_u32(uint32_t *p, int n, cudaStream_t st);
 cudaError_t count_keys(const uint32_t *keys, int n, int *counts, cudaStream_t st);
@@ -220,19 +223,14 @@ cudaError_t plan_dense_cells(const int *cell_start, int ncell, int64_t n_min, in
                              cudaStream_t st);
 
 // ---- kick / drift (nf_step.cu) ----
-// kick + drift of every particle, in storage order k: rec[2k] = new offset
-// (w 0), rec[2k + 1] = new velocity, ids[k] = perm[k], idx[k] = k, new_cell[k];
+// kick + drift of every particle into particle-id order: state_by_id[2 id] = new
+// offset (w holds the new cell id's bits), state_by_id[2 id + 1] = new velocity;
 // drift-limit violations counted in *cap_violations
 cudaError_t kick_drift(const float4 *pos, const float4 *vel, const double *acc64, const uint32_t *cell_of,
-                       const uint32_t *perm, double dt, double inv_w, int cpd, int n, float4 *rec, uint32_t *ids,
-                       uint32_t *idx, uint32_t *new_cell, int *cap_violations, cudaStream_t st);
-// keys[j] = new_cell[sidx[j]], vals[j] = j (id order; sidx[j]: storage index of
-// id j); counts += the new cells' occupancies
-cudaError_t drift_cell_keys(const uint32_t *sidx, const uint32_t *new_cell, int n, uint32_t *keys, uint32_t *vals,
-                            int *counts, cudaStream_t st);
-// pos[k], vel[k] = the record of id ids[k]
-cudaError_t drift_gather(const uint32_t *ids, const uint32_t *sidx, const float4 *rec, float4 *pos, float4 *vel, int n,
-                         cudaStream_t st);
+                       const uint32_t *perm, double dt, double inv_w, int cpd, int n, float4 *state_by_id,
+                       int *cap_violations, cudaStream_t st);
+// sort keys (new cell ids) and values (ids) from kick_drift's output; counts += cell occupancies
+cudaError_t drift_keys(const float4 *state_by_id, int n, uint32_t *keys, uint32_t *vals, int *counts, cudaStream_t st);
 
 // cell multipoles (nf_multipole.cu)
 // cut-off mode: the sub-cell moments of the dense cells (mpole, kCutSub * kCutWords floats per dense cell)

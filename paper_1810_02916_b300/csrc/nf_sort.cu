@@ -365,6 +365,26 @@ cudaError_t bin_global(const double *xyz, int n, int cpd, double inv_w, uint32_t
     return cudaGetLastError();
 }
 
+// the drift's records (offset with key bits, velocity) into storage order: one
+// 32-byte record read per particle
+__global__ void gather_state_kernel(const uint32_t *__restrict__ perm, const float4 *__restrict__ state_by_id,
+                                    float4 *__restrict__ pos, float4 *__restrict__ vel, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float4 *rec = state_by_id + 2 * static_cast<int64_t>(perm[k]);
+    const float4 q = rec[0];
+    pos[k] = make_float4(q.x, q.y, q.z, 0.f);   // w held the cell id's bits
+    vel[k] = rec[1];
+}
+
+cudaError_t gather_state(const uint32_t *perm, const float4 *state_by_id, float4 *pos, float4 *vel, int n,
+                         cudaStream_t st)
+{
+    gather_state_kernel<<<nblocks(n, 256), 256, 0, st>>>(perm, state_by_id, pos, vel, n);
+    return cudaGetLastError();
+}
+
 cudaError_t gather_sorted(const uint32_t *perm, const float4 *xq_by_id, const float4 *vel_by_id, float4 *pos,
                           float4 *vel, int n, cudaStream_t st)
 {

@@ -4,14 +4,12 @@
 // kick:  v' = v + a dt                  (a: the FP64 per-sink sums, box units)
 // drift: s = (c + 1/2 + x_rel) + v' dt cpd / box   per axis, in cell units,
 //        then the binning rule of nf_bin.cuh gives the new cell and offset.
-// One coalesced pass does both and writes, in storage order, one 32-byte record
-// per particle (new offset, new velocity), its id, its storage index and its
-// new cell.  The re-binning (nf_api.cu) then sorts (id, storage index) by id,
-// reads each particle's new cell in id order (cell_keys_by_id), sorts stably
-// by cell, and gathers the records (gather_records): every cell ends up ordered
-// by particle id, exactly as a fresh binning of the drifted positions would,
-// and no pass writes to scattered addresses.  The kick-drift pass writes
-// scratch only, so a step refused for its drift limit leaves the box as it was.
+// One pass does both and writes the new state in particle-id order, the new
+// cell id riding in the offset's w word; a second, coalesced pass lays the cell
+// ids out as sort keys (values: the ids) and counts the cells.  The stable sort
+// that follows then orders every cell by particle id, exactly as a fresh
+// binning of the drifted positions would.  The pass writes scratch only, so a
+// step refused for its drift limit leaves the box as it was.
 #include "nf_bin.cuh"
 #include "nf_internal.cuh"
 
@@ -23,8 +21,7 @@ inline int nblocks(int64_t n, int per) { return static_cast<int>((n + per - 1) /
 __global__ void kick_drift_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
                                   const double *__restrict__ acc64, const uint32_t *__restrict__ cell_of,
                                   const uint32_t *__restrict__ perm, double dt, double inv_w, int cpd, int n,
-                                  float4 *__restrict__ rec, uint32_t *__restrict__ ids, uint32_t *__restrict__ idx,
-                                  uint32_t *__restrict__ new_cell, int *__restrict__ violations)
+                                  float4 *__restrict__ state_by_id, int *__restrict__ violations)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -50,64 +47,42 @@ __global__ void kick_drift_kernel(const float4 *__restrict__ pos, const float4 *
     bin_cell_units(sx, cpd, nx, qx);
     bin_cell_units(sy, cpd, ny, qy);
     bin_cell_units(sz, cpd, nz, qz);
-    float4 *r = rec + 2 * static_cast<int64_t>(k);
-    r[0] = make_float4(qx, qy, qz, 0.f);
-    r[1] = make_float4(vx, vy, vz, 0.f);
-    ids[k] = perm[k];
-    idx[k] = static_cast<uint32_t>(k);
-    new_cell[k] = static_cast<uint32_t>((nx * cpd + ny) * cpd + nz);
+    const uint32_t id = perm[k];
+    const uint32_t key = static_cast<uint32_t>((nx * cpd + ny) * cpd + nz);
+    // one 32-byte record per particle (offset with the key bits, then the velocity), written by
+    // two adjacent 16-byte stores: the scattered writes fill whole 32-byte sectors
+    float4 *rec = state_by_id + 2 * static_cast<int64_t>(id);
+    rec[0] = make_float4(qx, qy, qz, __uint_as_float(key));   // key bits: moved, never computed with
+    rec[1] = make_float4(vx, vy, vz, 0.f);
 }
 
-// In id order j (sidx[j]: storage index of id j): the new cell as the sort key,
-// the id as the value; counts += the cells' occupancies
-__global__ void cell_keys_by_id(const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ new_cell, int n,
-                                uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, int *__restrict__ counts)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const uint32_t c = new_cell[sidx[j]];
-    keys[j] = c;
-    vals[j] = static_cast<uint32_t>(j);
-    atomicAdd(&counts[c], 1);
-}
-
-// The records into the new storage order (ids: the ids in that order)
-__global__ void gather_records(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ sidx,
-                               const float4 *__restrict__ rec, float4 *__restrict__ pos, float4 *__restrict__ vel,
-                               int n)
+__global__ void keys_from_state(const float4 *__restrict__ state_by_id, int n, uint32_t *__restrict__ keys,
+                                uint32_t *__restrict__ vals, int *__restrict__ counts)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const float4 *r = rec + 2 * static_cast<int64_t>(sidx[ids[k]]);
-    pos[k] = r[0];
-    vel[k] = r[1];
+    const uint32_t key = __float_as_uint(state_by_id[2 * static_cast<int64_t>(k)].w);
+    keys[k] = key;
+    vals[k] = static_cast<uint32_t>(k);
+    atomicAdd(&counts[key], 1);
 }
 
 }  // namespace
 
 cudaError_t kick_drift(const float4 *pos, const float4 *vel, const double *acc64, const uint32_t *cell_of,
-                       const uint32_t *perm, double dt, double inv_w, int cpd, int n, float4 *rec, uint32_t *ids,
-                       uint32_t *idx, uint32_t *new_cell, int *cap_violations, cudaStream_t st)
+                       const uint32_t *perm, double dt, double inv_w, int cpd, int n, float4 *state_by_id,
+                       int *cap_violations, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    kick_drift_kernel<<<nblocks(n, 256), 256, 0, st>>>(pos, vel, acc64, cell_of, perm, dt, inv_w, cpd, n, rec, ids,
-                                                       idx, new_cell, cap_violations);
+    kick_drift_kernel<<<nblocks(n, 256), 256, 0, st>>>(pos, vel, acc64, cell_of, perm, dt, inv_w, cpd, n,
+                                                       state_by_id, cap_violations);
     return cudaGetLastError();
 }
 
-cudaError_t drift_cell_keys(const uint32_t *sidx, const uint32_t *new_cell, int n, uint32_t *keys, uint32_t *vals,
-                            int *counts, cudaStream_t st)
+cudaError_t drift_keys(const float4 *state_by_id, int n, uint32_t *keys, uint32_t *vals, int *counts, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    cell_keys_by_id<<<nblocks(n, 256), 256, 0, st>>>(sidx, new_cell, n, keys, vals, counts);
-    return cudaGetLastError();
-}
-
-cudaError_t drift_gather(const uint32_t *ids, const uint32_t *sidx, const float4 *rec, float4 *pos, float4 *vel, int n,
-                         cudaStream_t st)
-{
-    if (n <= 0) return cudaSuccess;
-    gather_records<<<nblocks(n, 256), 256, 0, st>>>(ids, sidx, rec, pos, vel, n);
+    keys_from_state<<<nblocks(n, 256), 256, 0, st>>>(state_by_id, n, keys, vals, counts);
     return cudaGetLastError();
 }
 
