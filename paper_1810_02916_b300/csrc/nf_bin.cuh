@@ -20,10 +20,18 @@ __device__ __forceinline__ bool bin_cell_units(double s, int cpd, int &cell, flo
     const double rel = __dsub_rn(__dsub_rn(s, c), 0.5);
     const double q = rint(__dmul_rn(rel, kTwo22));
     xq = static_cast<float>(__dmul_rn(q, kTwoM22));
-    const double d = static_cast<double>(cpd);
-    const double cw = __dsub_rn(c, __dmul_rn(d, floor(__ddiv_rn(c, d))));
-    int ci = static_cast<int>(cw);
-    ci = ci < 0 ? ci + cpd : (ci >= cpd ? ci - cpd : ci);
+    int ci;
+    if (c >= -static_cast<double>(cpd) && c < 2.0 * static_cast<double>(cpd)) {
+        // within one box of the valid range (always after a drift): the wrap is one integer step,
+        // with no FP64 division (slow on this part's FP64 pipe); the same value as below
+        ci = static_cast<int>(c);
+        ci = ci < 0 ? ci + cpd : (ci >= cpd ? ci - cpd : ci);
+    } else {
+        const double d = static_cast<double>(cpd);
+        const double cw = __dsub_rn(c, __dmul_rn(d, floor(__ddiv_rn(c, d))));
+        ci = static_cast<int>(cw);
+        ci = ci < 0 ? ci + cpd : (ci >= cpd ? ci - cpd : ci);
+    }
     cell = ci;
     return true;
 }
