@@ -330,3 +330,28 @@ def test_tuner_keys_on_the_occupancy_profile():
     s = oracle.error_stats(b.forces()[:, :3], ref)
     assert s["rms_rel"] <= RMS_TOL, s
 
+
+
+def test_class_profile_accounts_for_every_item_and_pair():
+    """nf_profile(2): the per-class item counts and tiled pairs add up (lane items' pairs are
+    the rest), the clocks are positive where items ran, and the forces are the same as
+    without the profile."""
+    X, _ = gen.clustered(60000, np.random.default_rng(37), 5, 0.3 / 12, 1.5 / 12)
+    bg = np.random.default_rng(38).random((12 ** 3, 3))               # sparse background: lane items
+    X = np.concatenate([X, bg])
+    nf = make_box(X, 12, 1e-3)
+    plain = nf.forces()
+    nf.profile(2)
+    prof = nf.forces()
+    nf.profile_read()
+    raw = nf.profile_classes()
+    assert np.array_equal(plain, prof)
+    classes = {k: v for k, v in raw.items() if isinstance(v, tuple)}
+    assert sum(v[1] for v in classes.values()) > 0
+    tiled_pairs = sum(v[2] for k, v in classes.items() if not k.startswith("lane"))
+    assert classes["lane items"][1] > 0 and classes["lane items"][2] == 0
+    assert 0 < tiled_pairs < nf.pair_count()
+    for k, (cyc, items, _) in classes.items():
+        assert (cyc > 0) == (items > 0), k
+    assert raw["warps"] > 0 and raw["warp_lifetime_cycles"] >= sum(v[0] for v in classes.values())
+    assert nf.profile_classes()["warps"] == 0           # reading resets the sums
