@@ -78,9 +78,6 @@ namespace {
 #ifndef NF_ADJ_UNROLL
 #define NF_ADJ_UNROLL 4   // staged sources per unrolled step of the adjoint
 #endif
-#ifndef NF_VOTE_GROUP
-#define NF_VOTE_GROUP 1   // near sources per warp vote on 2- and 4-sink lanes (1 or 2)
-#endif
 #ifndef NF_PACKED_ADJ
 #define NF_PACKED_ADJ 1   // the adjoint evaluates two sinks per paired FP32 instruction on 2- and 4-sink lanes
 #endif
@@ -799,43 +796,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const float4 q = buf[j + u];
-                    if (VOTE && PACK && NF_VOTE_GROUP == 2) {
-                        // two sources per vote (fewer branches between the sources' chains)
-                        if (u & 1) continue;
-                        const float4 qb = buf[j + u + 1];
-                        float2 dx[2][SP], dy[2][SP], dz[2][SP], r2[2][SP];
-                        float m = 0.f;
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const float4 qh = h == 0 ? q : qb;
-                            const float2 qx = make_float2(qh.x, qh.x), qy = make_float2(qh.y, qh.y),
-                                         qz = make_float2(qh.z, qh.z);
-#pragma unroll
-                            for (int k = 0; k < SP; ++k) {
-                                dx[h][k] = __fadd2_rn(qx, nx2[k]);
-                                dy[h][k] = __fadd2_rn(qy, ny2[k]);
-                                dz[h][k] = __fadd2_rn(qz, nz2[k]);
-                                r2[h][k] = __ffma2_rn(dz[h][k], dz[h][k], __ffma2_rn(dy[h][k], dy[h][k],
-                                                      __ffma2_rn(dx[h][k], dx[h][k], make_float2(FLT_MIN, FLT_MIN))));
-                                const float mk = fminf(r2[h][k].x, r2[h][k].y);
-                                m = (h == 0 && k == 0) ? mk : fminf(m, mk);
-                            }
-                        }
-                        if (__any_sync(kFull, m < eps2)) {
-#pragma unroll
-                            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                                for (int k = 0; k < SP; ++k)
-                                    tail2_spline(dx[h][k], dy[h][k], dz[h][k], r2[h][k], ax2[k], ay2[k], az2[k], a02,
-                                                 a12, a22);
-                        } else {
-#pragma unroll
-                            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                                for (int k = 0; k < SP; ++k)
-                                    tail2_newton(dx[h][k], dy[h][k], dz[h][k], r2[h][k], ax2[k], ay2[k], az2[k]);
-                        }
-                    } else if (VOTE && PACK) {
+                    if (VOTE && PACK) {
                         // a near source takes the spline tail only when some sink of the
                         // warp lies within eps of it (self pairs included: r^2 = FLT_MIN)
                         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),

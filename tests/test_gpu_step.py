@@ -336,10 +336,10 @@ def test_class_profile_accounts_for_every_item_and_pair():
     """nf_profile(2): the per-class item counts and tiled pairs add up (lane items' pairs are
     the rest), the clocks are positive where items ran, and the forces are the same as
     without the profile."""
-    X, _ = gen.clustered(60000, np.random.default_rng(37), 5, 0.3 / 12, 1.5 / 12)
-    bg = np.random.default_rng(38).random((12 ** 3, 3))               # sparse background: lane items
+    X, _ = gen.clustered(12000, np.random.default_rng(37), 3, 0.2 / 16, 0.6 / 16)
+    bg = np.random.default_rng(38).random((2 * 16 ** 3, 3))           # sparse background: lane items
     X = np.concatenate([X, bg])
-    nf = make_box(X, 12, 1e-3)
+    nf = make_box(X, 16, 1e-3)
     plain = nf.forces()
     nf.profile(2)
     prof = nf.forces()
