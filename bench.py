@@ -423,7 +423,9 @@ def class_table(raw, pairs_total, launches, sm_mhz, warps_per_sm=24):
     busy_share: the class's share of the warps' summed busy cycles.  eff: pairs per warp-cycle
     against the FMA-lane bound shared by the resident warps (128 lanes / 14 ops per pair per SM
     cycle over warps_per_sm warps), i.e. how close the class runs to the roofline while it runs.
-    Lane items' pairs are the pass's total minus the tiled items' pairs."""
+    Lane items' pairs are the pass's total minus the tiled items' pairs.  busy_over_lifetime: busy
+    cycles over the warps' lifetimes (time spent taking items from the queue is the rest);
+    lifetime_over_wall: a warp's mean lifetime over one launch's wall time (the idle tail is the rest)."""
     per_warp_bound = FP32_LANES_PER_SM / FMA_OPS_PER_PAIR / warps_per_sm
     classes = {k: v for k, v in raw.items() if isinstance(v, tuple)}
     tiled_pairs = sum(v[2] for k, v in classes.items() if not k.startswith("lane"))
@@ -440,7 +442,7 @@ def class_table(raw, pairs_total, launches, sm_mhz, warps_per_sm=24):
     life = raw["warp_lifetime_cycles"]
     return dict(rows=rows, busy_over_lifetime=busy / max(life, 1), warps=raw["warps"] // launches,
                 wall_ms_per_launch=raw["wall_ns"] / 1e6 / launches,
-                lifetime_over_wall=life / max(raw["warps"], 1) / (raw["wall_ns"] * 1e-3 * sm_mhz)
+                lifetime_over_wall=life / max(raw["warps"], 1) / (raw["wall_ns"] / launches * 1e-3 * sm_mhz)
                 if raw["wall_ns"] else None)
 
 

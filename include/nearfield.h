@@ -138,11 +138,13 @@ double nf_spline_eps_from_plummer(double eps_plummer);
  *   xyz  n x 3 doubles, box units, any finite values (wrapped periodically);
  *        host or device pointer, particle id = row index
  *   n    number of particles, 0 <= n < 2^31
- * Each particle gets the cell c = floor(x cpd / box) per axis (wrapped) and
- * the offset x_rel = (x cpd / box - c) - 1/2 in cell widths, rounded to a
- * multiple of 2^-22 (half to even).  Particles are sorted by cell id, stably
+ * Each particle gets the cell c = floor(s) per axis (wrapped), s = x cpd / box
+ * in double, and the offset x_rel = (s - c) - 1/2 in cell widths, rounded once
+ * from its exact value to a multiple of 2^-22 (half to even; a negative
+ * offset that rounds to zero is -0).  Particles are sorted by cell id, stably
  * in id order.  Velocities are reset to zero.  NF_EINVAL for non-finite
- * positions.  Section 2.1 (cells, cell-centred positions).  Synchronises.
+ * positions or |x cpd / box| >= 2^52.  Section 2.1 (cells, cell-centred
+ * positions).  Synchronises.
  * A load that needs larger buffers than the box holds frees the old ones
  * first: if it then fails (NF_ENOMEM, or NF_EINVAL for the input), the box
  * is left empty rather than in its previous state.
@@ -227,10 +229,11 @@ int nf_get_forces64(nf_t *nf, double *acc);
 
 /*
  * nf_kick_drift -- one leapfrog kick and drift in FP64 arithmetic (Table 1,
- * rows Kick and Drift): v += a dt with a from the last nf_forces, then
- * x += v dt; positions are re-binned (new cells, offsets rounded to the
- * 2^-22 grid, stable sort by cell in id order).  Velocities and offsets are
- * stored as FP32.  If any particle would move more than 0.8 cell widths
+ * rows Kick and Drift): v' = fl32(v + a dt) with a the FP64 sums of the last
+ * nf_forces, then per axis s = (c + 1/2 + x_rel) + (v' dt) (cpd / box) in cell
+ * units with one FP64 rounding, re-binned by the rule of nf_bin_particles
+ * (new cells, offsets rounded once to the 2^-22 grid, stable sort by cell in
+ * id order).  Velocities and offsets are stored as FP32.  If any particle would move more than 0.8 cell widths
  * along an axis (the drift limit of Section 4.2.1) nothing is changed and
  * NF_EINVAL is returned.  NF_ESTATE without a previous nf_forces.
  * Synchronises.

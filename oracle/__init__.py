@@ -95,15 +95,32 @@ class Binned:
 
 
 def cell_coordinates(X: np.ndarray, cpd: int, box: float):
-    """Unwrapped integer cell coordinate and offset from the cell centre.
+    """Unwrapped integer cell coordinate and quantised offset from the cell centre.
 
-    s = X * (cpd / box) in double precision (one rounding each), c = floor(s),
-    x_rel = (s - c) - 1/2 in cell widths (both subtractions exact).
+    s = X * (cpd / box) in double precision (one rounding each) and c = floor(s).
+    The offset (s - c) - 1/2, in cell widths, is rounded once from its exact
+    value to a multiple of 2^-22, half to even; a negative offset that rounds
+    to zero keeps its sign, as rint does (Section 2.1: positions are kept as
+    offsets from their cell's centre; the paper fixes no grid, 2^-22 is a
+    reading that makes every cross-cell separation exact in FP32).
+
+    In quanta the exact offset is S - K with S = s 2^22 (an exact scaling) and
+    K = c 2^22 + 2^21, an even integer, so its rounding is rint(S) - K: adding
+    an even integer commutes with round-half-to-even.  rint(S) - c 2^22 is a
+    difference of two doubles that is exact (for |s| < 2^30 both are integers
+    below 2^52; beyond, both are integer-valued and within 2^22 of each other),
+    and subtracting 2^21 from the result is exact too.  Forming
+    (s - c) - 1/2 in double instead would round it a second time whenever
+    -1 < s < 1/4 and s has bits below 2^-53.
     """
     inv_w = float(cpd) / float(box)
     s = np.asarray(X, dtype=np.float64) * inv_w
     c = np.floor(s)
-    return c.astype(np.int64), (s - c) - 0.5
+    S = s * 2.0 ** QUANTUM_BITS
+    R = np.rint(S)
+    q = (R - c * 2.0 ** QUANTUM_BITS) - 2.0 ** (QUANTUM_BITS - 1)
+    q = np.where((q == 0) & (S < R), -0.0, q)          # rounded to zero from below
+    return c.astype(np.int64), (q * 2.0 ** -QUANTUM_BITS).astype(np.float32)
 
 
 def quantise(x_rel: np.ndarray) -> np.ndarray:
@@ -121,9 +138,9 @@ def bin_positions(X: np.ndarray, cpd: int, box: float = 1.0) -> Binned:
 
     Cell id = (cx cpd + cy) cpd + cz (x-major, z fastest); within a cell
     particles keep their input order (stable sort).  Cell-relative positions
-    are quantised with `quantise`.
+    are quantised as `cell_coordinates` states.
     """
-    c, xr = cell_coordinates(X, cpd, box)
+    c, xq = cell_coordinates(X, cpd, box)
     ci = np.mod(c, cpd)
     cell = (ci[:, 0] * cpd + ci[:, 1]) * cpd + ci[:, 2]
     order = np.argsort(cell, kind="stable")
@@ -131,7 +148,7 @@ def bin_positions(X: np.ndarray, cpd: int, box: float = 1.0) -> Binned:
     offsets = np.zeros(cpd ** 3 + 1, dtype=np.int64)
     np.cumsum(counts, out=offsets[1:])
     return Binned(cpd, float(box), order.astype(np.int64), cell[order].astype(np.int64),
-                  quantise(xr[order]), offsets, counts)
+                  xq[order], offsets, counts)
 
 
 def from_sorted(cpd: int, box: float, offsets: np.ndarray, xq: np.ndarray, order=None) -> Binned:

@@ -21,6 +21,12 @@ using nf::Reduce;
 
 static_assert(nf::kProfWords == NF_PROFILE_WORDS, "the header's profile size is out of date");
 
+// Source splitting aims at NF_BALANCE pieces of the pass per warp slot (32 per SM): no item much longer
+// than pairs / (SMs x 32 x NF_BALANCE), so the queue's last wave leaves little idle time
+#ifndef NF_BALANCE
+#define NF_BALANCE 4
+#endif
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -79,7 +85,7 @@ struct nf_box {
     int *nbr_all = nullptr;           // full 125-cell counts (lane-item choice in cut-off mode)
     float *mpole = nullptr;
     const int **nbr_ptr = nullptr;    // device copy of nbr's address (the split planner reads boxes' tables)
-    long long wf = 0;                 // resident warps (<= 32 per SM) x balance factor 4
+    long long wf = 0;                 // 32 warps per SM x the balance factor NF_BALANCE
     int reduce_cap = 0;
     void *dt_tmp = nullptr;           // time-step reductions
     unsigned long long *pairs = nullptr;
@@ -588,7 +594,7 @@ int nf_create(int cpd, int R, double eps, double box, nf_t **out)
         nf_destroy(nf);
         return rc;
     }
-    nf->wf = static_cast<long long>(nf->sm_count) * 32 * 4;
+    nf->wf = static_cast<long long>(nf->sm_count) * 32 * NF_BALANCE;
     e = cudaMemset(nf->cell_start, 0, cells);
     if (e == cudaSuccess) e = cudaMemset(nf->n_items, 0, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMemset(nf->n_reduce, 0, sizeof(int) * 4);

@@ -18,6 +18,12 @@ namespace {
 
 inline int nblocks(int64_t n, int per) { return static_cast<int>((n + per - 1) / per); }
 
+// (c + 1/2 + x_rel) 2^22 for a stored offset x_rel, a multiple of 2^-22 with |x_rel 2^22| <= 2^21 + 2
+__device__ __forceinline__ long long scaled_cell_position(int c, float x_rel)
+{
+    return (static_cast<long long>(c) << 22) + (1LL << 21) + static_cast<long long>(__float2int_rn(x_rel * 4194304.f));
+}
+
 __global__ void kick_drift_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
                                   const double *__restrict__ acc64, const uint32_t *__restrict__ cell_of,
                                   const uint32_t *__restrict__ perm, double dt, double inv_w, int cpd, int n,
@@ -35,18 +41,33 @@ __global__ void kick_drift_kernel(const float4 *__restrict__ pos, const float4 *
     const double my = __dmul_rn(__dmul_rn(static_cast<double>(vy), dt), inv_w);
     const double mz = __dmul_rn(__dmul_rn(static_cast<double>(vz), dt), inv_w);
     const double lim = 0.8;
-    if (!(fabs(mx) <= lim && fabs(my) <= lim && fabs(mz) <= lim)) atomicAdd(violations, 1);
+    const bool capped = fabs(mx) <= lim && fabs(my) <= lim && fabs(mz) <= lim;
+    if (!capped) atomicAdd(violations, 1);
     const uint32_t c = cell_of[k];
     const int cz = static_cast<int>(c % cpd), cy = static_cast<int>((c / cpd) % cpd), cx = static_cast<int>(c / (cpd * cpd));
     const float4 p = pos[k];
-    const double sx = __dadd_rn(static_cast<double>(cx) + 0.5 + static_cast<double>(p.x), mx);
-    const double sy = __dadd_rn(static_cast<double>(cy) + 0.5 + static_cast<double>(p.y), my);
-    const double sz = __dadd_rn(static_cast<double>(cz) + 0.5 + static_cast<double>(p.z), mz);
-    int nx, ny, nz;
-    float qx, qy, qz;
-    bin_cell_units(sx, cpd, nx, qx);
-    bin_cell_units(sy, cpd, ny, qy);
-    bin_cell_units(sz, cpd, nz, qz);
+    int nx = 0, ny = 0, nz = 0;
+    float qx = 0.f, qy = 0.f, qz = 0.f;
+    if (capped) {
+        // The stored position along an axis, s0 = c + 1/2 + x_rel in cell units, is an integer
+        // number of 2^-22 quanta (offsets are kept on that grid), so s0 2^22 is formed exactly in
+        // integers and S = s 2^22 = (s0 + m) 2^22 takes the drift's one FP64 rounding: m 2^22 is
+        // exact, and scaling by 2^22 commutes with rounding.
+        const double sx = __dadd_rn(static_cast<double>(scaled_cell_position(cx, p.x)), __dmul_rn(mx, kTwo22));
+        const double sy = __dadd_rn(static_cast<double>(scaled_cell_position(cy, p.y)), __dmul_rn(my, kTwo22));
+        const double sz = __dadd_rn(static_cast<double>(scaled_cell_position(cz, p.z)), __dmul_rn(mz, kTwo22));
+        bin_scaled(sx, cpd, nx, qx);
+        bin_scaled(sy, cpd, ny, qy);
+        bin_scaled(sz, cpd, nz, qz);
+    } else {
+        // a drift over the limit (reported): the same rule from s in FP64
+        const double sx = __dadd_rn(static_cast<double>(cx) + 0.5 + static_cast<double>(p.x), mx);
+        const double sy = __dadd_rn(static_cast<double>(cy) + 0.5 + static_cast<double>(p.y), my);
+        const double sz = __dadd_rn(static_cast<double>(cz) + 0.5 + static_cast<double>(p.z), mz);
+        bin_cell_units(sx, cpd, nx, qx);
+        bin_cell_units(sy, cpd, ny, qy);
+        bin_cell_units(sz, cpd, nz, qz);
+    }
     const uint32_t id = perm[k];
     const uint32_t key = static_cast<uint32_t>((nx * cpd + ny) * cpd + nz);
     // one 32-byte record per particle (offset with the key bits, then the velocity), written by

@@ -76,6 +76,56 @@ def test_one_kick_drift_step_matches_oracle():
     assert np.all(np.abs(_min_image(Xg - X1q)) <= ptol + 1e-15)
 
 
+def test_kick_drift_follows_the_fp64_rule_bit_for_bit():
+    """Every particle's new velocity, cell and offset equal the stated FP64 rule evaluated in NumPy
+    on the box's own state and FP64 forces: v' = fl32(v + a dt); s = (c + 1/2 + x_rel) + (v' dt) cpd;
+    new cell floor(s) wrapped, offset rounded once from (s - floor(s) - 1/2) 2^22, half to even.
+    A third of the particles get velocities that put the exact offset on a half-quantum tie."""
+    cpd, eps = 8, 1e-3                                   # cpd a power of two: cpd / box is exact
+    rng = np.random.default_rng(31)
+    X = rng.random((40000, 3))
+    nf = make_box(X, cpd, eps)
+    st0 = nf.get_particles()
+    n = nf.n
+    dt = 2.0 ** -30
+    # drifts m = v' dt cpd = v' 2^-27 cell widths, within the 0.8-cell limit
+    V = (np.clip(rng.standard_normal((n, 3)), -3.5, 3.5) * 0.2 * 2.0 ** 27).astype(np.float32)
+    tie = rng.random(n) < 1 / 3
+    j = rng.integers(-3_000_000, 3_000_000, (n, 3))
+    V[tie] = ((j[tie] + 0.5) * 32.0).astype(np.float32)     # m = (j + 1/2) 2^-22 when the kick adds nothing
+    vel = np.zeros((n, 4), np.float32)
+    vel[:, :3] = V
+    nf.set_velocities(vel)
+    nf.forces(False)
+    A = nf.forces64()
+    nf.kick_drift(dt)
+    st1 = nf.get_particles()
+    # expected, per storage index of the state before the step
+    v1 = (V.astype(np.float64) + A * dt).astype(np.float32)
+    m = (v1.astype(np.float64) * dt) * float(cpd)
+    cell0 = np.repeat(np.arange(cpd ** 3), st0["counts"].astype(np.int64))
+    c0 = np.stack([cell0 // (cpd * cpd), (cell0 // cpd) % cpd, cell0 % cpd], axis=1).astype(np.float64)
+    s = ((c0 + 0.5) + st0["pos"][:, :3].astype(np.float64)) + m
+    c1, q1 = oracle.cell_coordinates(s, 1, 1.0)             # cpd = box = 1: the coordinate is s itself
+    c1 = np.mod(c1, cpd)
+    cell1 = (c1[:, 0] * cpd + c1[:, 1]) * cpd + c1[:, 2]
+    # the state after the step, per particle id
+    ids0 = st0["perm"]
+    cell_after = np.repeat(np.arange(cpd ** 3), st1["counts"].astype(np.int64))
+    by_id_pos = np.empty((n, 3), np.float32)
+    by_id_vel = np.empty((n, 3), np.float32)
+    by_id_cell = np.empty(n, np.int64)
+    by_id_pos[st1["perm"]] = st1["pos"][:, :3]
+    by_id_vel[st1["perm"]] = st1["vel"][:, :3]
+    by_id_cell[st1["perm"]] = cell_after
+    assert np.array_equal(by_id_cell[ids0], cell1)
+    assert np.array_equal(by_id_pos[ids0].view(np.uint32), q1.view(np.uint32))
+    assert np.array_equal(by_id_vel[ids0].view(np.uint32), v1.view(np.uint32))
+    # the tie particles whose kick added nothing did land on ties, so the half-to-even rule was exercised
+    exact_tie = tie[:, None] & (v1 == V) & (np.abs(m) <= 0.8)
+    assert exact_tie.sum() > 10000
+
+
 def test_ten_steps_track_the_oracle_trajectory():
     """Ten leapfrog steps of a smooth system stay within a small multiple of the grid quantum."""
     cpd, eps = 6, 0.3 / 6

@@ -9,6 +9,7 @@ import os
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 import oracle
@@ -99,3 +100,32 @@ def test_pins_catch_mutant(name, old, new, checks, monkeypatch):
             except AssertionError:
                 failures += 1
         assert failures >= 1, f"no pin caught the mutant {name!r}"
+
+
+def _double_rounded_cell_coordinates(X, cpd, box):
+    """The binning rule with the offset formed as (s - c) - 1/2 in double, then rounded again."""
+    s = np.asarray(X, dtype=np.float64) * (float(cpd) / float(box))
+    c = np.floor(s)
+    return c.astype(np.int64), oracle.quantise((s - c) - 0.5)
+
+
+def _truncated_cell_coordinates(X, cpd, box):
+    """The binning rule with the offset truncated toward zero instead of rounded."""
+    s = np.asarray(X, dtype=np.float64) * (float(cpd) / float(box))
+    c = np.floor(s)
+    q = np.trunc(((s - c) - 0.5) * 2.0 ** 22) * 2.0 ** -22
+    return c.astype(np.int64), q.astype(np.float32)
+
+
+@pytest.mark.parametrize("mutant", [_double_rounded_cell_coordinates, _truncated_cell_coordinates],
+                         ids=["double-rounded offset", "truncated offset"])
+def test_binning_pins_catch_mutant(mutant, monkeypatch):
+    monkeypatch.setattr(oracle, "cell_coordinates", mutant)
+    failures = 0
+    for check in (pins.test_binning_rounds_each_offset_once_from_its_exact_value,
+                  pins.test_binning_matches_python_restatement):
+        try:
+            check()
+        except AssertionError:
+            failures += 1
+    assert failures >= 1, f"no pin caught the mutant {mutant.__name__}"

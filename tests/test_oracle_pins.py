@@ -7,6 +7,7 @@ brute-force code path, a symmetry, or finite differences.
 import json
 import math
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -217,6 +218,15 @@ def test_pair_count_two_ways():
 
 # ------------------------------------------------------------------ binning
 
+def _exact_offset(s):
+    """(floor(s), offset in quanta) for a double s: the offset (s - c - 1/2) 2^22 rounded half to
+    even in exact rational arithmetic, as a float that keeps the sign of a negative value rounded to 0."""
+    c = math.floor(s)
+    t = (Fraction(s) - c - Fraction(1, 2)) * 2 ** 22
+    q = round(t)                                  # Fraction rounding: half to even
+    return c, (-0.0 if (q == 0 and t < 0) else float(q))
+
+
 def _bin_python(X, cpd, box):
     """Per-particle pure-Python restatement of the binning rule (small inputs)."""
     inv_w = float(cpd) / float(box)
@@ -224,9 +234,8 @@ def _bin_python(X, cpd, box):
     for idx, p in enumerate(X.tolist()):
         cxyz, rel = [], []
         for v in p:
-            s = v * inv_w
-            c = math.floor(s)
-            rel.append(round(((s - c) - 0.5) * 2 ** 22) / 2 ** 22)   # Python round: half to even
+            c, q = _exact_offset(v * inv_w)
+            rel.append(q / 2 ** 22)
             cxyz.append(c % cpd)
         cell = (cxyz[0] * cpd + cxyz[1]) * cpd + cxyz[2]
         rows.append((cell, idx, rel))
@@ -250,6 +259,35 @@ def test_binning_matches_python_restatement():
     assert np.array_equal(b.xq.astype(np.float64), np.array([r[2] for r in rows]))
     assert int(b.offsets[-1]) == 400 and np.array_equal(np.diff(b.offsets), b.counts)
     assert np.all(np.abs(b.xq) <= 0.5)
+
+
+def test_binning_rounds_each_offset_once_from_its_exact_value():
+    """Offsets bit for bit against exact rational rounding, where a double-precision (s - c) - 1/2
+    would round twice: -1 < s < 1/4 with bits below 2^-53, half-quantum ties, offsets that round to
+    -0, and coordinates far outside the box."""
+    q22 = 2.0 ** -22
+    s_vals = [
+        -(2.5 + 2.0 ** -40) * q22,        # double rounding lands on a tie that breaks the wrong way
+        -(1.5 + 2.0 ** -40) * q22, (0.5 - 2.0 ** -40) * q22, 3.5 * q22, -3.5 * q22,
+        2.0 ** -60, -2.0 ** -60, 5e-324, -5e-324, 0.0, -0.0,
+        0.5 - 0.3 * q22, 0.5 + 0.3 * q22, 0.5 - 0.5 * q22, 0.5 + 0.5 * q22, 1.5 - 0.5 * q22,
+        0.25 - 2.0 ** -70, 0.125 + 2.0 ** -80, -0.75 + 2.0 ** -70, 2.0 ** 31 + 0.5 - 2.0 ** -22,
+        -(2.0 ** 33) - 0.25, 1e9 + 0.5, -1e9 - 0.75,
+    ]
+    rng = np.random.default_rng(41)
+    s_vals += (rng.uniform(-1, 1, 300) * 2.0 ** rng.integers(-60, 0, 300)).tolist()
+    s_vals += (rng.uniform(-3, 3, 300)).tolist()
+    s = np.array(s_vals, dtype=np.float64)
+    c, xq = oracle.cell_coordinates(s[:, None], 1, 1.0)      # cpd = box = 1: the coordinate is s itself
+    for k, v in enumerate(s_vals):
+        ce, qe = _exact_offset(v)
+        assert int(c[k, 0]) == ce, v
+        want = np.float32(qe * q22)
+        assert xq[k, 0].view(np.uint32) == want.view(np.uint32), (v, float(xq[k, 0]) / q22, qe)
+    # the first case separates the two roundings: a double (s - c) - 1/2 gives one quantum more
+    v = s_vals[0]
+    twice = np.rint((((v - math.floor(v)) - 0.5)) * 2.0 ** 22)
+    assert twice == _exact_offset(v)[1] + 1
 
 
 def test_quantised_offsets_make_fp32_separations_exact():
