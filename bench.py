@@ -39,9 +39,11 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "zeldovich512"
 METRIC = "near-field Gpair-interactions/s and particles/s/step at 512^3 clustered vs plain FP32 kernel"
 UNIT = "Gpair/s"
-# FP32 FMA-pipe lane operations per pair at r >= eps (3 sub, 3 for r^2, 5 for the Newton-refined r^-3,
-# 3 accumulate): the least the law needs for a pair outside the softening length, i.e. nearly every pair
-FMA_OPS_PER_PAIR = 14
+# FP32 FMA-pipe lane operations per pair at r >= eps (3 sub, 3 for r^2, 4 for the Newton-refined r^-3 in the
+# accumulators' scale: y^2, r^2 y^2 - A, y^3, their product; 3 accumulate): the least the law needs for a pair
+# outside the softening length, i.e. nearly every pair, and what the kernel executes for such a pair
+FMA_OPS_PER_PAIR = 13
+PREVIOUS_OPS_PER_PAIR = 14   # the same with the Newton factor 1 + 3e formed on its own (2 ops instead of 1)
 BRANCH_FREE_OPS_PER_PAIR = 18   # the same with the law evaluated branch-free, min(r^-3, g(r)), for every pair
 ISSUE_OPS_PER_PAIR = 20    # FP32-pipe instructions per pair of the branch-free law issued one lane-op at a time
 # DRAM bytes (read + write) of one compensated pair-kernel launch of this workload: the mean of the
@@ -352,6 +354,7 @@ def run(args):
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak_gps = props.multi_processor_count * sm_max * 1e6 * FP32_LANES_PER_SM / FMA_OPS_PER_PAIR / 1e9
+    peak14_gps = props.multi_processor_count * sm_max * 1e6 * FP32_LANES_PER_SM / PREVIOUS_OPS_PER_PAIR / 1e9
     issue_peak_gps = props.multi_processor_count * sm_max * 1e6 * FP32_LANES_PER_SM / ISSUE_OPS_PER_PAIR / 1e9
     branch_free_peak_gps = (props.multi_processor_count * sm_max * 1e6 * FP32_LANES_PER_SM /
                             BRANCH_FREE_OPS_PER_PAIR / 1e9)
@@ -374,13 +377,16 @@ def run(args):
                           frac=pair_kernel_gps / peak_gps, traffic=_pair_traffic(),
                           traffic_note="DRAM read+write bytes of one pair-kernel launch (ncu, same workload); "
                                        "algorithmic bytes: positions 2.15 GB read + FP64 sums 3.22 GB written",
+                          frac_14_ops=pair_kernel_gps / peak14_gps,
                           branch_free_frac=pair_kernel_gps / branch_free_peak_gps,
                           issue_convention_frac=pair_kernel_gps / issue_peak_gps,
                           paper_convention_frac=pair_kernel_gps * 23 /
                           (props.multi_processor_count * sm_max * 1e-3 * FP32_LANES_PER_SM * 2),
                           peak_basis=f"FP32 FMA-lane roofline: {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
                                      f"({src}) x 128 lanes / {FMA_OPS_PER_PAIR} FMA-pipe ops per pair (Newtonian "
-                                     "pair, one Newton step); branch_free_frac: the same over "
+                                     "pair, one Newton step); frac_14_ops: the same over "
+                                     f"{PREVIOUS_OPS_PER_PAIR} ops (the Newton factor formed on its own); "
+                                     "branch_free_frac: the same over "
                                      f"{BRANCH_FREE_OPS_PER_PAIR} ops (min(r^-3, g) for every pair); "
                                      f"issue_convention_frac: over {ISSUE_OPS_PER_PAIR} single-lane instructions per "
                                      "pair of the branch-free law; paper_convention_frac: 23 FLOP per pair against "
@@ -421,7 +427,7 @@ def class_table(raw, pairs_total, launches, sm_mhz, warps_per_sm=24):
     """Per-item-class breakdown of the pair kernel (profile mode 2).
 
     busy_share: the class's share of the warps' summed busy cycles.  eff: pairs per warp-cycle
-    against the FMA-lane bound shared by the resident warps (128 lanes / 14 ops per pair per SM
+    against the FMA-lane bound shared by the resident warps (128 lanes / 13 ops per pair per SM
     cycle over warps_per_sm warps), i.e. how close the class runs to the roofline while it runs.
     Lane items' pairs are the pass's total minus the tiled items' pairs.  busy_over_lifetime: busy
     cycles over the warps' lifetimes (time spent taking items from the queue is the rest);

@@ -7,6 +7,19 @@
 
 namespace nf {
 
+// Scale of the pair kernel's force accumulators: they hold kForceSigma times
+// the acceleration (cell units), kForceSigma = -(A - 1) with A = 13981013 *
+// 2^-23, the FP32 value nearest 5/3 (so A - 1 = 11184810 * 2^-24 is exact in
+// FP32).  The Newtonian tail then needs no separate Newton factor: with y the
+// SFU estimate of (r^2)^-1/2 and h = r^2 y^2 = 1 - 2e, one Newton step gives
+// r^-3 = y^3 (1 + 3e), and y^3 (h - A) = -y^3 (A - 1 + 2e) equals kForceSigma
+// y^3 (1 + 3e) up to a relative 3e (2/(3(A - 1)) - 1) < 2^-43.  Every force
+// path (spline and Plummer laws, cut-off moments) accumulates in this scale;
+// the FP64 result is multiplied by kForceUnscale.  The adjoint is unscaled.
+constexpr float kNewtonA = 1.66666662693023681640625f;
+constexpr float kForceSigma = -0.666666626930236816406250f;
+constexpr double kForceUnscale = 1.0 / -0.666666626930236816406250;
+
 // Near-field radius supported by the kernels (Section 2.1: R = 2, 125 cells).
 constexpr int kR = 2;
 constexpr int kNbr = (2 * kR + 1) * (2 * kR + 1) * (2 * kR + 1);   // 125

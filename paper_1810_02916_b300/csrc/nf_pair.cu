@@ -26,17 +26,19 @@
 //     sums are combined with a fixed xor-shuffle tree;
 //   * pair arithmetic is FP32, rsqrt on the SFU plus one Newton step.  A far
 //     source (Chebyshev distance 2, so r >= 1 cell > eps) takes f = r^-3 with
-//     the Newton step folded into the cube: 14 FP32 FMA-pipe operations + 1
-//     SFU.  A near source takes the same 14 unless some sink of the warp lies
-//     within eps of it (a warp vote on r^2 < eps^2, which self pairs always
-//     trigger); then all of the warp's pairs with it take the branch-free law,
-//     18 operations + 1 min + 1 SFU.  Lanes holding 2 or 4 sinks evaluate two
+//     the Newton step folded into the cube and the accumulators' scale
+//     (kForceSigma): 13 FP32 FMA-pipe operations + 1 SFU.  A near source takes
+//     the same 13 unless some sink of the warp lies within eps of it (a warp
+//     vote on r^2 < eps^2, which self pairs always trigger); then all of the
+//     warp's pairs with it take the branch-free law, 19 operations + 1 min + 1
+//     SFU.  Lanes holding 2 or 4 sinks evaluate two
 //     sinks per paired FP32 instruction (FADD2 / FMUL2 / FFMA2), which halves
 //     the issue slots so the FP32 lanes, not instruction issue, bound the loop;
 //   * accumulation: plain FFMA within a round (<= B sources), folded after
 //     every round into a (hi, lo) pair with an exact two-sum and reduced to
 //     FP64 per sink at the end (compensated mode); or one FP32 running sum
-//     per sink (plain mode).
+//     per sink (plain mode).  The sums carry the factor kForceSigma, which
+//     the FP64 conversion removes.
 //
 // Exactness of separations: offsets are multiples of 2^-22 cell widths with
 // |x| <= 1/2, so x_j + D (|D| <= 2) and (x_j + D) - x_i are exact in FP32.
@@ -145,7 +147,7 @@ __device__ __forceinline__ void tail_spline(float dx, float dy, float dz, float 
     const float r = fmaf(t, e, t);           // r2 * y
     const float y3 = y * y * y;
     const float g = fmaf(fmaf(a2, r, a1), r, a0);
-    const float f = fminf(y3, g);
+    const float f = fminf(y3, g) * kForceSigma;   // the accumulators' scale
     ax = fmaf(f, dx, ax);
     ay = fmaf(f, dy, ay);
     az = fmaf(f, dz, az);
@@ -155,39 +157,32 @@ __device__ __forceinline__ void tail_spline(float dx, float dy, float dz, float 
 // r^-3 itself: with y the SFU estimate of (r^2)^-1/2 and h = r^2 y^2, one
 // Newton step for (r^2)^-1/2 multiplies y by 1 + e, e = (1 - h) / 2, so
 // r^-3 = y^3 (1 + e)^3 = y^3 (1 + 3e) + O(e^2) (|e| < 2^-21, the dropped
-// terms below 2^-40 relative).  8 FP32-pipe operations + 1 SFU, no min.
+// terms below 2^-40 relative).  In the accumulators' scale kForceSigma =
+// -(A - 1) that is y^3 (h - A) (nf_internal.cuh): one FFMA forms h - A, so
+// the pair costs 7 FP32-pipe operations + 1 SFU, no min.
 __device__ __forceinline__ void tail_newton(float dx, float dy, float dz, float r2, float &ax, float &ay, float &az)
 {
-    const float y = rsqrtf(r2);              // SFU
+    const float y = rsqrtf(r2);                   // SFU
     const float yy = y * y;
-    const float h = r2 * yy;
-    const float y3 = yy * y;
-    const float e3 = fmaf(h, -1.5f, 1.5f);   // 3e
-    const float f = fmaf(y3, e3, y3);
+    const float g = fmaf(r2, yy, -kNewtonA);      // h - A
+    const float f = (yy * y) * g;                 // kForceSigma r^-3
     ax = fmaf(f, dx, ax);
     ay = fmaf(f, dy, ay);
     az = fmaf(f, dz, az);
 }
 
-// one pair: a += f(r) d.  Spline (SOFT = 0): f = min(r^-3, a0 + a1 r + a2 r^2),
-// 20 FP32-pipe operations + 1 SFU.  Plummer (SOFT = 1, Eq. eqn:plummer):
-// f = (r^2 + eps_p^2)^-3/2, 15 FP32-pipe operations + 1 SFU (eps2 = eps_p^2).
+// one pair: a += kForceSigma f(r) d.  Spline (SOFT = 0): f = min(r^-3, a0 +
+// a1 r + a2 r^2), 21 FP32-pipe operations + 1 SFU.  Plummer (SOFT = 1, Eq.
+// eqn:plummer): f = (r^2 + eps_p^2)^-3/2, 13 FP32-pipe operations + 1 SFU
+// (eps2 = eps_p^2).
 template <int SOFT>
 __device__ __forceinline__ void pair_force(const float4 q, float xi, float yi, float zi, float &ax, float &ay,
                                            float &az, float a0, float a1, float a2, float eps2)
 {
     const float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
     if (SOFT == 1) {
-        const float s2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-        float y = rsqrtf(s2);
-        const float t = s2 * y;
-        const float h = t * y;
-        const float e = fmaf(h, -0.5f, 0.5f);
-        y = fmaf(y, e, y);
-        const float f = y * y * y;
-        ax = fmaf(f, dx, ax);
-        ay = fmaf(f, dy, ay);
-        az = fmaf(f, dz, az);
+        // (r^2 + eps_p^2)^-3/2 in the accumulators' scale, the Newton step taken on the cube
+        tail_newton(dx, dy, dz, fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2))), ax, ay, az);
         return;
     }
     // + FLT_MIN: below half an ulp of any nonzero r^2 on the 2^-22 grid (r^2 >= 2^-44), so it changes
@@ -210,7 +205,8 @@ __device__ __forceinline__ void tail2_spline(const float2 dx, const float2 dy, c
     const float2 r = __ffma2_rn(t, e, t);
     const float2 y3 = __fmul2_rn(__fmul2_rn(y, y), y);
     const float2 g = __ffma2_rn(__ffma2_rn(a2, r, a1), r, a0);
-    const float2 f = make_float2(fminf(y3.x, g.x), fminf(y3.y, g.y));
+    const float2 f = __fmul2_rn(make_float2(fminf(y3.x, g.x), fminf(y3.y, g.y)),
+                                make_float2(kForceSigma, kForceSigma));   // the accumulators' scale
     ax = __ffma2_rn(f, dx, ax);
     ay = __ffma2_rn(f, dy, ay);
     az = __ffma2_rn(f, dz, az);
@@ -222,10 +218,8 @@ __device__ __forceinline__ void tail2_newton(const float2 dx, const float2 dy, c
 {
     const float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
     const float2 yy = __fmul2_rn(y, y);
-    const float2 h = __fmul2_rn(r2, yy);
-    const float2 y3 = __fmul2_rn(yy, y);
-    const float2 e3 = __ffma2_rn(h, make_float2(-1.5f, -1.5f), make_float2(1.5f, 1.5f));
-    const float2 f = __ffma2_rn(y3, e3, y3);
+    const float2 g = __ffma2_rn(r2, yy, make_float2(-kNewtonA, -kNewtonA));   // h - A
+    const float2 f = __fmul2_rn(__fmul2_rn(yy, y), g);                         // kForceSigma r^-3
     ax = __ffma2_rn(f, dx, ax);
     ay = __ffma2_rn(f, dy, ay);
     az = __ffma2_rn(f, dz, az);
@@ -242,18 +236,8 @@ __device__ __forceinline__ void pair_force2(const float2 qx, const float2 qy, co
                                             const float2 a0, const float2 a1, const float2 a2, const float2 eps2)
 {
     const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
-    const float2 half = make_float2(0.5f, 0.5f), mhalf = make_float2(-0.5f, -0.5f);
     if (SOFT == 1) {
-        const float2 s2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
-        float2 y = make_float2(rsqrtf(s2.x), rsqrtf(s2.y));
-        const float2 t = __fmul2_rn(s2, y);
-        const float2 h = __fmul2_rn(t, y);
-        const float2 e = __ffma2_rn(h, mhalf, half);
-        y = __ffma2_rn(y, e, y);
-        const float2 f = __fmul2_rn(__fmul2_rn(y, y), y);
-        ax = __ffma2_rn(f, dx, ax);
-        ay = __ffma2_rn(f, dy, ay);
-        az = __ffma2_rn(f, dz, az);
+        tail2_newton(dx, dy, dz, __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2))), ax, ay, az);
         return;
     }
     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(FLT_MIN, FLT_MIN))));
@@ -262,7 +246,7 @@ __device__ __forceinline__ void pair_force2(const float2 qx, const float2 qy, co
 
 // One pair with a source in a cell at Chebyshev distance 2 from the sink's
 // cell: r >= 1 cell width > eps, so the spline law is Newtonian there and the
-// pair takes tail_newton: 14 FP32-pipe operations + 1 SFU.
+// pair takes tail_newton: 13 FP32-pipe operations + 1 SFU.
 __device__ __forceinline__ void pair_force_far(const float4 q, float xi, float yi, float zi, float &ax, float &ay,
                                                float &az)
 {
@@ -950,9 +934,10 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
 #pragma unroll
                 for (int s = 0; s < SS; ++s) quad_force(cx - sxp[s], cy - syp[s], cz - szp[s], M, o + 4, mx[s], my[s], mz[s]);
             }
-            // one FP32 partial per dense cell, folded like a round of sources
+            // one FP32 partial per dense cell, in the accumulators' scale, folded like a round of sources
 #pragma unroll
             for (int s = 0; s < SS; ++s) {
+                mx[s] *= kForceSigma; my[s] *= kForceSigma; mz[s] *= kForceSigma;
                 if (COMP) {
                     comp_fold_smem(comp + lane + 32 * s, mx[s], my[s], mz[s]);
                 } else {
@@ -1001,7 +986,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         }
         return src_hi - src_lo;
     }
-    const double scale = ADJ ? bx.grad_scale : bx.acc_scale;
+    const double scale = ADJ ? bx.grad_scale : bx.acc_scale * kForceUnscale;
 #pragma unroll
     for (int s = 0; s < SS; ++s) {
         const int k = SPLIT ? lane : lane + 32 * s;
@@ -1125,7 +1110,7 @@ __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
             }
         }
     }
-    const double scale = ADJ ? bx.grad_scale : bx.acc_scale;
+    const double scale = ADJ ? bx.grad_scale : bx.acc_scale * kForceUnscale;
     const double gx = (static_cast<double>(acc.hx) + static_cast<double>(acc.lx)) * scale;
     const double gy = (static_cast<double>(acc.hy) + static_cast<double>(acc.ly)) * scale;
     const double gz = (static_cast<double>(acc.hz) + static_cast<double>(acc.lz)) * scale;

@@ -333,7 +333,7 @@ __global__ void reduce_kernel(const BoxDev *__restrict__ boxes, const Reduce *__
         a[1] += q[1];
         a[2] += q[2];
     }
-    const double scale = adjoint ? bx.grad_scale : bx.acc_scale;
+    const double scale = adjoint ? bx.grad_scale : bx.acc_scale * kForceUnscale;   // forces: accumulators' scale
     const int idx = rd.sink_begin + k;
     const double gx = a[0] * scale, gy = a[1] * scale, gz = a[2] * scale;
     if (bx.acc64) {
