@@ -312,6 +312,7 @@ void fill_box_desc(nf_t *nf, BoxDev &b, float4 *acc_out, double *acc64, const fl
     b.partials = nf->partials;
     b.cpd = nf->cpd;
     b.n = static_cast<int>(nf->n);
+    b.zcell = 1;   // every load and re-binning writes the cell's z index into pos[k].w
     b.a0 = static_cast<float>(10.0 / (ec * ec * ec));
     b.a1 = static_cast<float>(-15.0 / (ec * ec * ec * ec));
     b.a2 = static_cast<float>(6.0 / (ec * ec * ec * ec * ec));
@@ -409,11 +410,11 @@ int sort_and_gather(nf_t *nf, int src, bool with_vel)
                                key_bits(nf->ncell), nf->radix_tmp, &in_alt, nf->stream));
     nf->cur = in_alt ? 1 - src : src;
     if (with_vel)
-        NF_CK(nf::gather_state(nf->vals[nf->cur], nf->state_by_id, nf->pos, nf->vel, static_cast<int>(nf->n),
-                               nf->stream));
+        NF_CK(nf::gather_state(nf->vals[nf->cur], nf->keys[nf->cur], nf->cpd, nf->state_by_id, nf->pos, nf->vel,
+                               static_cast<int>(nf->n), nf->stream));
     else
-        NF_CK(nf::gather_sorted(nf->vals[nf->cur], nf->xq_by_id, nullptr, nf->pos, nf->vel, static_cast<int>(nf->n),
-                                nf->stream));
+        NF_CK(nf::gather_sorted(nf->vals[nf->cur], nf->keys[nf->cur], nf->cpd, nf->xq_by_id, nullptr, nf->pos,
+                                nf->vel, static_cast<int>(nf->n), nf->stream));
     return NF_OK;
 }
 
@@ -472,6 +473,14 @@ __global__ void k_perm64(const uint32_t *v, int n, int64_t *out)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) out[k] = v[k];
+}
+__global__ void k_pos_out(const float4 *pos, int n, float4 *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        const float4 p = pos[k];
+        out[k] = make_float4(p.x, p.y, p.z, 0.f);
+    }
 }
 
 inline int nblk(int64_t n) { return static_cast<int>((n + 255) / 256); }
@@ -764,7 +773,8 @@ int nf_set_particles(nf_t *nf, const int64_t *cell_offsets, const int32_t *count
     std::swap(nf->pos, nf->xq_by_id);
     nf->n = n;
     NF_CK(nf::iota_u32(nf->vals[nf->cur], static_cast<int>(n), nf->stream));
-    NF_CK(nf::fill_cell_ids(nf->cell_start, nf->ncell, static_cast<int>(n), nf->keys[nf->cur], nf->stream));
+    NF_CK(nf::fill_cell_ids(nf->cell_start, nf->ncell, static_cast<int>(n), nf->keys[nf->cur], nf->pos, nf->cpd,
+                            nf->stream));
     NF_CK(cudaMemsetAsync(nf->vel, 0, sizeof(float4) * static_cast<size_t>(n < 1 ? 1 : n), nf->stream));
     if ((rc = plan(nf))) return rc;
     nf->box_dirty = true;
@@ -811,7 +821,16 @@ int nf_get_particles(nf_t *nf, int64_t *cell_offsets, int32_t *counts, float *po
         });
         if (rc) return rc;
     }
-    if (pos && n > 0) NF_CK(cudaMemcpyAsync(pos, nf->pos, sizeof(float4) * n, cudaMemcpyDefault, st));
+    // the stored w holds the cell's z index; the caller gets the documented pad 0
+    const bool pos_on_host = pos && n > 0 && !(is_device_ptr(pos) && aligned16(pos));
+    if (pos && n > 0) {
+        if (pos_on_host) {
+            NF_CK(cudaMemcpyAsync(pos, nf->pos, sizeof(float4) * n, cudaMemcpyDefault, st));
+        } else {
+            k_pos_out<<<nblk(n), 256, 0, st>>>(nf->pos, n, reinterpret_cast<float4 *>(pos));
+            NF_CK(cudaGetLastError());
+        }
+    }
     if (vel && n > 0) NF_CK(cudaMemcpyAsync(vel, nf->vel, sizeof(float4) * n, cudaMemcpyDefault, st));
     if (perm && n > 0) {
         rc = produce_out(nf, perm, sizeof(int64_t) * n, [&](void *d) -> int {
@@ -822,6 +841,8 @@ int nf_get_particles(nf_t *nf, int64_t *cell_offsets, int32_t *counts, float *po
         if (rc) return rc;
     }
     NF_CK(cudaStreamSynchronize(st));
+    if (pos_on_host)
+        for (int64_t k = 0; k < n; ++k) pos[4 * k + 3] = 0.f;
     return NF_OK;
 }
 

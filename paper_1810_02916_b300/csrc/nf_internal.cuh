@@ -46,6 +46,7 @@ struct BoxDev {
     double *partials;         // FP64 partial sums of split items, cell units
     int cpd;
     int n;
+    int zcell;                // 1: pos[k].w holds the z index of particle k's cell (boxes the library loads)
     float a0, a1, a2;         // spline g(r) = a0 + a1 r + a2 r^2 in cell units
     float eps2;               // eps^2 in cell units (spline: adjoint branch test; Plummer: eps_p^2)
     double acc_scale;         // (cpd / box)^2: cell-unit acceleration -> box units
@@ -174,14 +175,17 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
                              int key_bits, void *temp, int *result_in_alt, cudaStream_t st);
 cudaError_t bin_global(const double *xyz, int n, int cpd, double inv_w, uint32_t *key, uint32_t *val,
                        float4 *xq_by_id, int *counts, int *err, cudaStream_t st);
-cudaError_t gather_sorted(const uint32_t *perm, const float4 *xq_by_id, const float4 *vel_by_id, float4 *pos,
-                          float4 *vel, int n, cudaStream_t st);
+// storage order from per-id offsets: pos[k] = (xq_by_id[perm[k]].xyz, z index of cell keys[k])
+cudaError_t gather_sorted(const uint32_t *perm, const uint32_t *keys, int cpd, const float4 *xq_by_id,
+                          const float4 *vel_by_id, float4 *pos, float4 *vel, int n, cudaStream_t st);
 cudaError_t validate_loaded(const int64_t *offsets, const int32_t *counts, const float4 *pos, int ncell, int n,
                             int *cell_start, float4 *pos_out, int *err, cudaStream_t st);
-// storage order from the drift's per-id records (state_by_id: 2 float4 per id)
-cudaError_t gather_state(const uint32_t *perm, const float4 *state_by_id, float4 *pos, float4 *vel, int n,
-                         cudaStream_t st);
-cudaError_t fill_cell_ids(const int *cell_start, int ncell, int n, uint32_t *cell_of, cudaStream_t st);
+// storage order from the drift's per-id records (state_by_id: 2 float4 per id); pos w as gather_sorted
+cudaError_t gather_state(const uint32_t *perm, const uint32_t *keys, int cpd, const float4 *state_by_id, float4 *pos,
+                         float4 *vel, int n, cudaStream_t st);
+// cell_of[k] = the cell holding storage index k; with pos, also pos[k].w = that cell's z index
+cudaError_t fill_cell_ids(const int *cell_start, int ncell, int n, uint32_t *cell_of, float4 *pos, int cpd,
+                          cudaStream_t st);
 cudaError_t iota_u32(uint32_t *p, int n, cudaStream_t st);
 cudaError_t count_keys(const uint32_t *keys, int n, int *counts, cudaStream_t st);
 

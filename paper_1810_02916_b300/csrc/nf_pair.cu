@@ -92,6 +92,9 @@ namespace {
 #ifndef NF_PAIR_UNROLL
 #define NF_PAIR_UNROLL 2   // source pairs per unrolled step on lanes holding one sink
 #endif
+#ifndef NF_LANE_PAIRED
+#define NF_LANE_PAIRED 1   // lane items of library-loaded boxes: z offsets from w, two sources per paired instruction
+#endif
 #ifndef NF_UNROLL_S2
 #define NF_UNROLL_S2 NF_SRC_UNROLL   // staged sources per unrolled step on lanes holding two sinks
 #endif
@@ -1007,6 +1010,104 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
     return src_hi - src_lo;
 }
 
+// Forces of a lane item when every stored position carries its cell's z index
+// in w (BoxDev::zcell, boxes the library loaded).  Each lane walks its 25
+// (dx, dy) columns as run_lanes does, but a source's z offset is w + zoff (an
+// exact small integer; zoff is constant over a column's run, which does not
+// wrap), so a column needs only the two cell boundaries of its run, and each
+// lane evaluates two consecutive sources per paired FP32 instruction (an odd
+// last source is paired with far-away padding, an exact zero).  Separations
+// stay exact: (w + zoff) - x_i and x_j + that are sums on the 2^-22 grid below
+// 4 in magnitude.  Columns at |dx| = 2 or |dy| = 2 take the Newtonian law;
+// in the others a source pair takes the branch-free law only when one of its
+// pairs lies within eps (self pairs included: r^2 = FLT_MIN).
+template <bool COMP, int SOFT>
+__device__ void run_lanes_paired(const BoxDev &bx, const Item &item, int lane)
+{
+    const int count = item_count(item);
+    if (lane >= count) return;
+    const int C = bx.cpd;
+    const int *cs = bx.cell_start;
+    const int g0 = item.cell, ng = item_lane_cells(item);
+    const int i = item.sink_begin + lane;
+    int c = g0;   // the sink's cell: the last of the run starting at or before i
+    for (int k = 1; k < ng; ++k) c += __ldg(cs + g0 + k) <= i;
+    const int cz = c % C, cy = (c / C) % C, cx = c / (C * C);
+    const float4 p = __ldg(bx.pos + i);
+    const float eps2 = bx.eps2;
+    const float2 a02 = make_float2(bx.a0, bx.a0), a12 = make_float2(bx.a1, bx.a1), a22 = make_float2(bx.a2, bx.a2);
+    const float2 e22 = make_float2(eps2, eps2), fmin2 = make_float2(FLT_MIN, FLT_MIN);
+    const float2 npz = make_float2(-p.z, -p.z);
+    Comp3 acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const bool wrap_lo = cz < 2, wrap_hi = cz + 3 > C;   // never both: C >= 5
+    for (int col = 0; col < 25; ++col) {
+        const int dxi = col / 5 - 2, dyi = col % 5 - 2;
+        int nx = cx + dxi, ny = cy + dyi;
+        nx += nx < 0 ? C : 0; nx -= nx >= C ? C : 0;
+        ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
+        const int *row = cs + (nx * C + ny) * C;
+        const float ox = static_cast<float>(dxi) - p.x, oy = static_cast<float>(dyi) - p.y;   // exact
+        const float2 ox2 = make_float2(ox, ox), oy2 = make_float2(oy, oy);
+        // warp-uniform (every lane walks the columns in the same order)
+        const bool far_col = dxi == -2 || dxi == 2 || dyi == -2 || dyi == 2;
+        float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+        for (int part = 0; part < 2; ++part) {
+            // cells [z0, z1) of the row; a source in cell z lies at z offset z + zoff
+            int z0, z1, zoff;
+            if (part == 0) {
+                z0 = wrap_lo ? cz - 2 + C : cz - 2;
+                z1 = wrap_lo ? C : min(cz + 3, C);
+                zoff = wrap_lo ? -cz - C : -cz;
+            } else {
+                if (!wrap_lo && !wrap_hi) break;
+                z0 = 0;
+                z1 = wrap_lo ? cz + 3 : cz + 3 - C;
+                zoff = wrap_lo ? -cz : C - cz;
+            }
+            const int j0 = __ldg(row + z0), j1 = __ldg(row + z1);
+            const float2 zo2 = make_float2(static_cast<float>(zoff), static_cast<float>(zoff));
+            for (int j = j0; j < j1; j += 2) {
+                const float4 q0 = __ldg(bx.pos + j);
+                const float4 q1 = j + 1 < j1 ? __ldg(bx.pos + j + 1) : make_float4(kFar, kFar, kFar, 0.f);
+                const float2 dx = __fadd2_rn(make_float2(q0.x, q1.x), ox2);
+                const float2 dy = __fadd2_rn(make_float2(q0.y, q1.y), oy2);
+                // (w + zoff) is the integer z offset; minus x_i, plus x_j: each step exact
+                const float2 dzi = __fadd2_rn(__fadd2_rn(make_float2(q0.w, q1.w), zo2), npz);
+                const float2 dz = __fadd2_rn(make_float2(q0.z, q1.z), dzi);
+                if (SOFT == 1) {
+                    tail2_newton(dx, dy, dz, __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e22))), ax,
+                                 ay, az);
+                } else {
+                    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, fmin2)));
+                    if (!far_col && fminf(r2.x, r2.y) < eps2)
+                        tail2_spline(dx, dy, dz, r2, ax, ay, az, a02, a12, a22);
+                    else
+                        tail2_newton(dx, dy, dz, r2, ax, ay, az);
+                }
+            }
+        }
+        const float px = ax.x + ax.y, py = ay.x + ay.y, pz = az.x + az.y;
+        if (COMP) {
+            float s, e;
+            two_sum(acc.hx, px, s, e); acc.hx = s; acc.lx = __fadd_rn(acc.lx, e);
+            two_sum(acc.hy, py, s, e); acc.hy = s; acc.ly = __fadd_rn(acc.ly, e);
+            two_sum(acc.hz, pz, s, e); acc.hz = s; acc.lz = __fadd_rn(acc.lz, e);
+        } else {
+            acc.hx += px; acc.hy += py; acc.hz += pz;
+        }
+    }
+    const double scale = bx.acc_scale * kForceUnscale;
+    const double gx = (static_cast<double>(acc.hx) + static_cast<double>(acc.lx)) * scale;
+    const double gy = (static_cast<double>(acc.hy) + static_cast<double>(acc.ly)) * scale;
+    const double gz = (static_cast<double>(acc.hz) + static_cast<double>(acc.lz)) * scale;
+    if (bx.acc64) {
+        double *o = bx.acc64 + 3 * static_cast<int64_t>(i);
+        o[0] = gx; o[1] = gy; o[2] = gz;
+    }
+    if (bx.acc_out)
+        bx.acc_out[i] = make_float4(static_cast<float>(gx), static_cast<float>(gy), static_cast<float>(gz), 0.f);
+}
+
 // A lane item (a run of sparse cells, <= 32 sinks): every lane takes one sink
 // against its own neighbourhood, read straight from global memory (L1) as the
 // 25 (dx, dy) columns of five z-cells.  The five cells of a column are one
@@ -1171,7 +1272,10 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
         const long long t0 = prof ? clock64() : 0;
         int kind, srcs = 0;
         if (item_is_lanes(item)) {
-            run_lanes<COMP, ADJ, SOFT>(bx, item, lane);
+            if (!ADJ && NF_LANE_PAIRED && bx.zcell)
+                run_lanes_paired<COMP, SOFT>(bx, item, lane);
+            else
+                run_lanes<COMP, ADJ, SOFT>(bx, item, lane);
             kind = 4;
         } else if (cnt <= 16) {
             srcs = run_item<0, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);

@@ -234,15 +234,22 @@ __global__ void bin_global_kernel(const double *__restrict__ xyz, int n, int cpd
     atomicAdd(&counts[c], 1);
 }
 
-__global__ void gather_kernel(const uint32_t *__restrict__ perm, const float4 *__restrict__ xq_by_id,
-                              const float4 *__restrict__ vel_by_id, float4 *__restrict__ pos,
-                              float4 *__restrict__ vel, int n)
+// w of a stored position: the z index of its cell (cell ids are x-major, z fastest), an
+// integer below 2^24 and so exact in FP32; lane items take each source's z offset from it
+__device__ __forceinline__ float cell_z(uint32_t cell, int cpd)
+{
+    return static_cast<float>(cell % static_cast<uint32_t>(cpd));
+}
+
+__global__ void gather_kernel(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ keys, int cpd,
+                              const float4 *__restrict__ xq_by_id, const float4 *__restrict__ vel_by_id,
+                              float4 *__restrict__ pos, float4 *__restrict__ vel, int n)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const uint32_t i = perm[k];
     const float4 q = xq_by_id[i];
-    pos[k] = make_float4(q.x, q.y, q.z, 0.f);   // w: scratch (the drift's cell id) before the sort
+    pos[k] = make_float4(q.x, q.y, q.z, cell_z(keys[k], cpd));
     if (vel) vel[k] = vel_by_id ? vel_by_id[i] : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
@@ -286,7 +293,8 @@ __global__ void validate_pos(const float4 *__restrict__ pos, int n, float4 *__re
     out[k] = make_float4(q[0], q[1], q[2], 0.f);
 }
 
-__global__ void cell_ids_kernel(const int *__restrict__ cell_start, int ncell, int n, uint32_t *__restrict__ cell_of)
+__global__ void cell_ids_kernel(const int *__restrict__ cell_start, int ncell, int n, uint32_t *__restrict__ cell_of,
+                                float4 *__restrict__ pos, int cpd)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -296,6 +304,7 @@ __global__ void cell_ids_kernel(const int *__restrict__ cell_start, int ncell, i
         if (cell_start[mid] <= k) lo = mid; else hi = mid;
     }
     cell_of[k] = static_cast<uint32_t>(lo);
+    if (pos) pos[k].w = cell_z(static_cast<uint32_t>(lo), cpd);
 }
 
 __global__ void count_keys_kernel(const uint32_t *__restrict__ keys, int n, int *__restrict__ counts)
@@ -367,29 +376,30 @@ cudaError_t bin_global(const double *xyz, int n, int cpd, double inv_w, uint32_t
 
 // the drift's records (offset with key bits, velocity) into storage order: one
 // 32-byte record read per particle
-__global__ void gather_state_kernel(const uint32_t *__restrict__ perm, const float4 *__restrict__ state_by_id,
-                                    float4 *__restrict__ pos, float4 *__restrict__ vel, int n)
+__global__ void gather_state_kernel(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ keys, int cpd,
+                                    const float4 *__restrict__ state_by_id, float4 *__restrict__ pos,
+                                    float4 *__restrict__ vel, int n)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const float4 *rec = state_by_id + 2 * static_cast<int64_t>(perm[k]);
     const float4 q = rec[0];
-    pos[k] = make_float4(q.x, q.y, q.z, 0.f);   // w held the cell id's bits
+    pos[k] = make_float4(q.x, q.y, q.z, cell_z(keys[k], cpd));   // the record's w held the cell id's bits
     vel[k] = rec[1];
 }
 
-cudaError_t gather_state(const uint32_t *perm, const float4 *state_by_id, float4 *pos, float4 *vel, int n,
-                         cudaStream_t st)
+cudaError_t gather_state(const uint32_t *perm, const uint32_t *keys, int cpd, const float4 *state_by_id, float4 *pos,
+                         float4 *vel, int n, cudaStream_t st)
 {
-    gather_state_kernel<<<nblocks(n, 256), 256, 0, st>>>(perm, state_by_id, pos, vel, n);
+    gather_state_kernel<<<nblocks(n, 256), 256, 0, st>>>(perm, keys, cpd, state_by_id, pos, vel, n);
     return cudaGetLastError();
 }
 
-cudaError_t gather_sorted(const uint32_t *perm, const float4 *xq_by_id, const float4 *vel_by_id, float4 *pos,
-                          float4 *vel, int n, cudaStream_t st)
+cudaError_t gather_sorted(const uint32_t *perm, const uint32_t *keys, int cpd, const float4 *xq_by_id,
+                          const float4 *vel_by_id, float4 *pos, float4 *vel, int n, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    gather_kernel<<<nblocks(n, 256), 256, 0, st>>>(perm, xq_by_id, vel_by_id, pos, vel, n);
+    gather_kernel<<<nblocks(n, 256), 256, 0, st>>>(perm, keys, cpd, xq_by_id, vel_by_id, pos, vel, n);
     return cudaGetLastError();
 }
 
@@ -402,10 +412,11 @@ cudaError_t validate_loaded(const int64_t *offsets, const int32_t *counts, const
     return cudaGetLastError();
 }
 
-cudaError_t fill_cell_ids(const int *cell_start, int ncell, int n, uint32_t *cell_of, cudaStream_t st)
+cudaError_t fill_cell_ids(const int *cell_start, int ncell, int n, uint32_t *cell_of, float4 *pos, int cpd,
+                          cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    cell_ids_kernel<<<nblocks(n, 256), 256, 0, st>>>(cell_start, ncell, n, cell_of);
+    cell_ids_kernel<<<nblocks(n, 256), 256, 0, st>>>(cell_start, ncell, n, cell_of, pos, cpd);
     return cudaGetLastError();
 }
 
