@@ -95,6 +95,12 @@ namespace {
 #ifndef NF_LANE_PAIRED
 #define NF_LANE_PAIRED 1   // lane items of library-loaded boxes: z offsets from w, two sources per paired instruction
 #endif
+#ifndef NF_LANE_PREFETCH
+#define NF_LANE_PREFETCH 0   // paired lane items load the next column's cell bounds during the current column
+#endif
+#ifndef NF_LANE_PAIR_UNROLL
+#define NF_LANE_PAIR_UNROLL 2   // paired lane items: source pairs per unrolled step (1 or 2)
+#endif
 #ifndef NF_UNROLL_S2
 #define NF_UNROLL_S2 NF_SRC_UNROLL   // staged sources per unrolled step on lanes holding two sinks
 #endif
@@ -1040,12 +1046,30 @@ __device__ void run_lanes_paired(const BoxDev &bx, const Item &item, int lane)
     const float2 npz = make_float2(-p.z, -p.z);
     Comp3 acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const bool wrap_lo = cz < 2, wrap_hi = cz + 3 > C;   // never both: C >= 5
-    for (int col = 0; col < 25; ++col) {
-        const int dxi = col / 5 - 2, dyi = col % 5 - 2;
-        int nx = cx + dxi, ny = cy + dyi;
+    // the first run of every column spans cells [zr0, zr1) of the column's row
+    const int zr0 = wrap_lo ? cz - 2 + C : cz - 2, zr1 = wrap_lo ? C : min(cz + 3, C);
+    auto row_of = [&](int col) {
+        int nx = cx + col / 5 - 2, ny = cy + col % 5 - 2;
         nx += nx < 0 ? C : 0; nx -= nx >= C ? C : 0;
         ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
-        const int *row = cs + (nx * C + ny) * C;
+        return cs + (nx * C + ny) * C;
+    };
+    // NF_LANE_PREFETCH: the next column's first-run bounds are loaded while this column runs
+    int jn0 = 0, jn1 = 0;
+    if (NF_LANE_PREFETCH) {
+        const int *row0 = row_of(0);
+        jn0 = __ldg(row0 + zr0);
+        jn1 = __ldg(row0 + zr1);
+    }
+    for (int col = 0; col < 25; ++col) {
+        const int dxi = col / 5 - 2, dyi = col % 5 - 2;
+        const int *row = row_of(col);
+        int jc0 = jn0, jc1 = jn1;
+        if (NF_LANE_PREFETCH && col + 1 < 25) {
+            const int *rown = row_of(col + 1);
+            jn0 = __ldg(rown + zr0);
+            jn1 = __ldg(rown + zr1);
+        }
         const float ox = static_cast<float>(dxi) - p.x, oy = static_cast<float>(dyi) - p.y;   // exact
         const float2 ox2 = make_float2(ox, ox), oy2 = make_float2(oy, oy);
         // warp-uniform (every lane walks the columns in the same order)
@@ -1064,14 +1088,19 @@ __device__ void run_lanes_paired(const BoxDev &bx, const Item &item, int lane)
                 z1 = wrap_lo ? cz + 3 : cz + 3 - C;
                 zoff = wrap_lo ? -cz : C - cz;
             }
-            const int j0 = __ldg(row + z0), j1 = __ldg(row + z1);
+            int j0, j1;
+            if (NF_LANE_PREFETCH && part == 0) {
+                j0 = jc0;
+                j1 = jc1;
+            } else {
+                j0 = __ldg(row + z0);
+                j1 = __ldg(row + z1);
+            }
             const float2 zo2 = make_float2(static_cast<float>(zoff), static_cast<float>(zoff));
-            for (int j = j0; j < j1; j += 2) {
-                const float4 q0 = __ldg(bx.pos + j);
-                const float4 q1 = j + 1 < j1 ? __ldg(bx.pos + j + 1) : make_float4(kFar, kFar, kFar, 0.f);
+            // one source pair: (w + zoff) is the integer z offset; minus x_i, plus x_j: each step exact
+            auto pair = [&](const float4 &q0, const float4 &q1) {
                 const float2 dx = __fadd2_rn(make_float2(q0.x, q1.x), ox2);
                 const float2 dy = __fadd2_rn(make_float2(q0.y, q1.y), oy2);
-                // (w + zoff) is the integer z offset; minus x_i, plus x_j: each step exact
                 const float2 dzi = __fadd2_rn(__fadd2_rn(make_float2(q0.w, q1.w), zo2), npz);
                 const float2 dz = __fadd2_rn(make_float2(q0.z, q1.z), dzi);
                 if (SOFT == 1) {
@@ -1083,6 +1112,25 @@ __device__ void run_lanes_paired(const BoxDev &bx, const Item &item, int lane)
                         tail2_spline(dx, dy, dz, r2, ax, ay, az, a02, a12, a22);
                     else
                         tail2_newton(dx, dy, dz, r2, ax, ay, az);
+                }
+            };
+            const float4 pad = make_float4(kFar, kFar, kFar, 0.f);
+            if (NF_LANE_PAIR_UNROLL == 2) {
+                // two source pairs per step, their four loads issued together; a second pair
+                // with no source left is skipped
+                for (int j = j0; j < j1; j += 4) {
+                    const float4 q0 = __ldg(bx.pos + j);
+                    const float4 q1 = j + 1 < j1 ? __ldg(bx.pos + j + 1) : pad;
+                    const float4 q2 = j + 2 < j1 ? __ldg(bx.pos + j + 2) : pad;
+                    const float4 q3 = j + 3 < j1 ? __ldg(bx.pos + j + 3) : pad;
+                    pair(q0, q1);
+                    if (j + 2 < j1) pair(q2, q3);
+                }
+            } else {
+                for (int j = j0; j < j1; j += 2) {
+                    const float4 q0 = __ldg(bx.pos + j);
+                    const float4 q1 = j + 1 < j1 ? __ldg(bx.pos + j + 1) : pad;
+                    pair(q0, q1);
                 }
             }
         }
