@@ -76,10 +76,10 @@ __host__ __device__ inline int item_lane_cells(const Item &it) { return -1 - it.
 // neighbourhood are computed through lane items (runs of at most kLaneMaxCells
 // cells and 32 sinks); kLaneMaxN = 0 turns lane items off.
 #ifndef NF_LANE_MAX_N
-#define NF_LANE_MAX_N 8
+#define NF_LANE_MAX_N 16
 #endif
 #ifndef NF_LANE_MAX_T
-#define NF_LANE_MAX_T 512
+#define NF_LANE_MAX_T 1000
 #endif
 constexpr int kLaneMaxN = NF_LANE_MAX_N;
 constexpr int kLaneMaxT = NF_LANE_MAX_T;
@@ -109,6 +109,7 @@ constexpr int kCutWords = 10;
 // smallest n_min: a dense cell then holds more particles than a lane cell's whole
 // 125-cell neighbourhood may (kLaneMaxT), so no lane item has a dense cell in reach
 constexpr int kCutMinN = 1024;
+static_assert(kLaneMaxT < kCutMinN, "a lane cell's neighbourhood must be smaller than any dense cell");
 
 // How a cell's sinks are cut into work items (its sink tiles): floor(n / 128)
 // full tiles of 128 sinks, then the remainder r (0 < r < 128): one tile of r

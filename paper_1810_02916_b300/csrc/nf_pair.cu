@@ -101,6 +101,12 @@ namespace {
 #ifndef NF_LANE_PAIR_UNROLL
 #define NF_LANE_PAIR_UNROLL 2   // paired lane items: source pairs per unrolled step (1 or 2)
 #endif
+#ifndef NF_SHIFT_TABLE
+#define NF_SHIFT_TABLE 1   // the shift pass reads each entry's cell offset from a per-block table
+#endif
+#ifndef NF_FOLD_HALVES
+#define NF_FOLD_HALVES 1   // one-sink lanes add their two source-pair halves before the compensated fold
+#endif
 #ifndef NF_UNROLL_S2
 #define NF_UNROLL_S2 NF_SRC_UNROLL   // staged sources per unrolled step on lanes holding two sinks
 #endif
@@ -530,8 +536,35 @@ __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float
 // the round is then rewritten in place as three arrays x[B], y[B], z[B] (the
 // layout the source-paired loops read two sources at a time from)
 template <int B, bool SOA>
-__device__ __forceinline__ void stage_shift(float4 *buf, int lane, const unsigned char *ts)
+__device__ __forceinline__ void stage_shift(float4 *buf, int lane, const unsigned char *ts, const float4 *offtab)
 {
+    if (NF_SHIFT_TABLE) {
+        // offtab[t1]: the cell offset of table code t1 - 1 (offtab[0] = 0 for padding entries)
+        float4 v[B / 32];
+#pragma unroll
+        for (int m = 0; m < B / 32; ++m) {
+            const float4 o = offtab[ts[m * 32 + lane]];
+            v[m] = buf[m * 32 + lane];
+            v[m].x += o.x;
+            v[m].y += o.y;
+            v[m].z += o.z;
+        }
+        if constexpr (SOA) {
+            __syncwarp();   // every lane has read its entries before any array entry is written over them
+            float *xs = reinterpret_cast<float *>(buf);
+#pragma unroll
+            for (int m = 0; m < B / 32; ++m) {
+                const int slot = m * 32 + lane;
+                xs[slot] = v[m].x;
+                xs[B + slot] = v[m].y;
+                xs[2 * B + slot] = v[m].z;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < B / 32; ++m) buf[m * 32 + lane] = v[m];
+        }
+        return;
+    }
     if constexpr (SOA) {
         float4 v[B / 32];
 #pragma unroll
@@ -586,7 +619,7 @@ __device__ __forceinline__ void comp_fold_smem(float *c, float &px, float &py, f
 // number of sources the item evaluated for each of its sinks.
 template <int S, int B, bool COMP, bool ADJ, int SOFT>
 __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float4 *wstage, int *tstart, int *tpre,
-                         float *comp, unsigned char *tslot, int lane)
+                         float *comp, unsigned char *tslot, const float4 *offtab, int lane)
 {
     constexpr bool SPLIT = (S == 0);
     constexpr int SS = SPLIT ? 1 : S;
@@ -688,7 +721,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         // the shift pass reads entries other lanes copied (contiguous staging): their copies are
         // complete once each lane has passed its wait
         if (NF_STAGE_CONTIG) __syncwarp();
-        stage_shift<B, PAIRSRC>(buf, lane, tslot + (r & 1) * B);
+        stage_shift<B, PAIRSRC>(buf, lane, tslot + (r & 1) * B, offtab);
         __syncwarp();
         const int nr = min(B, src_hi - src_lo - r * B);
         // this round's entries [0, nn) come from the 27 near cells and take the
@@ -882,8 +915,15 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         }
         if (COMP) {
             if (PAIRSRC) {
-                comp_fold_smem(comp + lane, ax2[0].x, ay2[0].x, az2[0].x);
-                comp_fold_smem(comp + lane, ax2[0].y, ay2[0].y, az2[0].y);
+                if (NF_FOLD_HALVES) {
+                    // the two halves' sum rounds once per round, within the round's FP32 partial error
+                    float hx = ax2[0].x + ax2[0].y, hy = ay2[0].x + ay2[0].y, hz = az2[0].x + az2[0].y;
+                    comp_fold_smem(comp + lane, hx, hy, hz);
+                    ax2[0] = ay2[0] = az2[0] = make_float2(0.f, 0.f);
+                } else {
+                    comp_fold_smem(comp + lane, ax2[0].x, ay2[0].x, az2[0].x);
+                    comp_fold_smem(comp + lane, ax2[0].y, ay2[0].y, az2[0].y);
+                }
             } else if (PACK || PACKA) {
 #pragma unroll
                 for (int k = 0; k < SP; ++k) {
@@ -1271,6 +1311,8 @@ __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
         bx.acc_out[i] = make_float4(static_cast<float>(gx), static_cast<float>(gy), static_cast<float>(gz), 0.f);
 }
 
+constexpr int kOffTab = 128;   // entries of the per-block cell-offset table (codes 0..124, plus one)
+
 // per-warp shared memory, in float4 units: staged sources (and cotangents),
 // compensated sums, neighbour table (256 ints), table slots (2 B bytes)
 template <int B, bool COMP, bool ADJ>
@@ -1302,6 +1344,18 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
     int *tabs = reinterpret_cast<int *>(w0 + (ADJ ? 4 : 2) * B + (COMP ? 192 : 0));
     int *tstart = tabs, *tpre = tabs + 128;
     unsigned char *tslot = reinterpret_cast<unsigned char *>(tabs + 256);
+    // after every warp's area: the cell offset of each neighbour-table code (index code + 1; 0: padding)
+    float4 *offtab = smem_f4 + (blockDim.x >> 5) * per_warp_f4<B, COMP, ADJ>();
+    if (NF_SHIFT_TABLE) {
+        for (int t1 = threadIdx.x; t1 < kOffTab; t1 += blockDim.x) {
+            const int t = t1 - 1;
+            offtab[t1] = t1 == 0 || t1 > kNbr ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                              : make_float4(static_cast<float>(t / 25 - 2),
+                                                            static_cast<float>((t / 5) % 5 - 2),
+                                                            static_cast<float>(t % 5 - 2), 0.f);
+        }
+        __syncthreads();
+    }
     const int n_items = *n_items_p;
     long long life0 = 0;
     unsigned long long wall0 = 0;
@@ -1326,16 +1380,20 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
                 run_lanes<COMP, ADJ, SOFT>(bx, item, lane);
             kind = 4;
         } else if (cnt <= 16) {
-            srcs = run_item<0, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            srcs = run_item<0, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, offtab,
+                                                          lane);
             kind = 3;
         } else if (cnt <= 32) {
-            srcs = run_item<1, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            srcs = run_item<1, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, offtab,
+                                                          lane);
             kind = 2;
         } else if (cnt <= 64) {
-            srcs = run_item<2, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            srcs = run_item<2, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, offtab,
+                                                          lane);
             kind = 1;
         } else {
-            srcs = run_item<4, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, lane);
+            srcs = run_item<4, B, COMP, ADJ, SOFT>(bx, item, stage, wstage, tstart, tpre, comp, tslot, offtab,
+                                                          lane);
             kind = 0;
         }
         __syncwarp();
@@ -1357,7 +1415,8 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
 template <int B, bool COMP, bool ADJ>
 size_t smem_bytes(int warps)
 {
-    return static_cast<size_t>(warps) * per_warp_f4<B, COMP, ADJ>() * sizeof(float4);
+    return (static_cast<size_t>(warps) * per_warp_f4<B, COMP, ADJ>() + (NF_SHIFT_TABLE ? kOffTab : 0)) *
+           sizeof(float4);
 }
 
 // Occupancy of one instantiation at `warps` warps per block on the current

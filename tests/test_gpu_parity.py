@@ -341,13 +341,13 @@ def test_sparse_cells_lane_items(mode):
 
 
 def test_lane_items_mixed_occupancy():
-    """Cells of 0..8 particles: lane runs that end at a tiled cell, at 32 sinks, at 32
-    cells (a long empty stretch) and at the row end, next to tiled cells; spline and
-    Plummer laws."""
+    """Cells of 0..24 particles (lane cells hold at most 16 and see at most 1000 sources):
+    lane runs that end at a tiled cell, at 32 sinks, at 32 cells (a long empty stretch)
+    and at the row end, next to tiled cells; spline and Plummer laws."""
     import paper_1810_02916_b300 as nfb
     cpd = 11
     rng = np.random.default_rng(41)
-    counts = rng.choice([0, 0, 1, 1, 2, 3, 4, 4, 5, 8], size=cpd ** 3)
+    counts = rng.choice([0, 0, 1, 1, 2, 3, 4, 4, 5, 8, 12, 16, 17, 24], size=cpd ** 3)
     counts[3 * cpd * cpd: 3 * cpd * cpd + 40] = 0                  # 40 empty cells in a row
     counts[5 * cpd * cpd + 2 * cpd: 5 * cpd * cpd + 3 * cpd] = 4     # a row of 44 sinks in lane cells
     cells = np.repeat(np.arange(cpd ** 3), counts)
