@@ -107,6 +107,9 @@ namespace {
 #ifndef NF_FOLD_HALVES
 #define NF_FOLD_HALVES 1   // one-sink lanes add their two source-pair halves before the compensated fold
 #endif
+#ifndef NF_PAIRED_FOLD
+#define NF_PAIRED_FOLD 1   // lanes with 2 or 4 sinks fold two sinks' partials per paired FP32 instruction
+#endif
 #ifndef NF_UNROLL_S2
 #define NF_UNROLL_S2 NF_SRC_UNROLL   // staged sources per unrolled step on lanes holding two sinks
 #endif
@@ -603,9 +606,39 @@ __device__ __forceinline__ void stage_shift(float4 *buf, int lane, const unsigne
     }
 }
 
-// Compensated sums live in shared memory (per warp: 6 x 128 floats, slot =
-// sink slot of the lane), so the registers hold only positions and the
-// running FP32 partials of the current round.
+// Compensated sums live in shared memory (per warp: 6 x 128 floats, word
+// comp_slot(lane, s) of each array for the lane's sink s), so the registers
+// hold only positions and the running FP32 partials of the current round.
+// With NF_PAIRED_FOLD the sinks 2k and 2k + 1 of a lane are adjacent words,
+// so both fold with paired FP32 instructions (each half exactly the scalar
+// two-sum).
+__device__ __forceinline__ int comp_slot(int lane, int s)
+{
+    return NF_PAIRED_FOLD ? 2 * lane + 64 * (s >> 1) + (s & 1) : lane + 32 * s;
+}
+
+// a - b with one rounding (b times -1 is exact inside the fused operation)
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = __fadd2_rn(a, b);
+    const float2 bp = fsub2(s, a);
+    const float2 ap = fsub2(s, bp);
+    e = __fadd2_rn(fsub2(a, ap), fsub2(b, bp));
+}
+
+// fold the partials of sinks 2k, 2k + 1 (c = comp + comp_slot(lane, 2k))
+__device__ __forceinline__ void comp_fold_smem2(float *c, float2 &px, float2 &py, float2 &pz)
+{
+    float2 *h = reinterpret_cast<float2 *>(c);
+    float2 s, e;
+    two_sum2(h[0], px, s, e); h[0] = s; h[192] = __fadd2_rn(h[192], e);
+    two_sum2(h[64], py, s, e); h[64] = s; h[256] = __fadd2_rn(h[256], e);
+    two_sum2(h[128], pz, s, e); h[128] = s; h[320] = __fadd2_rn(h[320], e);
+    px = py = pz = make_float2(0.f, 0.f);
+}
+
 __device__ __forceinline__ void comp_fold_smem(float *c, float &px, float &py, float &pz)
 {
     float s, e;
@@ -648,7 +681,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         }
         px[s] = py[s] = pz[s] = 0.f;
         if (COMP) {
-            float *c = comp + lane + 32 * s;
+            float *c = comp + comp_slot(lane, s);
 #pragma unroll
             for (int q = 0; q < 6; ++q) c[128 * q] = 0.f;
         }
@@ -918,21 +951,25 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
                 if (NF_FOLD_HALVES) {
                     // the two halves' sum rounds once per round, within the round's FP32 partial error
                     float hx = ax2[0].x + ax2[0].y, hy = ay2[0].x + ay2[0].y, hz = az2[0].x + az2[0].y;
-                    comp_fold_smem(comp + lane, hx, hy, hz);
+                    comp_fold_smem(comp + comp_slot(lane, 0), hx, hy, hz);
                     ax2[0] = ay2[0] = az2[0] = make_float2(0.f, 0.f);
                 } else {
-                    comp_fold_smem(comp + lane, ax2[0].x, ay2[0].x, az2[0].x);
-                    comp_fold_smem(comp + lane, ax2[0].y, ay2[0].y, az2[0].y);
+                    comp_fold_smem(comp + comp_slot(lane, 0), ax2[0].x, ay2[0].x, az2[0].x);
+                    comp_fold_smem(comp + comp_slot(lane, 0), ax2[0].y, ay2[0].y, az2[0].y);
                 }
             } else if (PACK || PACKA) {
 #pragma unroll
                 for (int k = 0; k < SP; ++k) {
-                    comp_fold_smem(comp + lane + 32 * (2 * k), ax2[k].x, ay2[k].x, az2[k].x);
-                    comp_fold_smem(comp + lane + 32 * (2 * k + 1), ax2[k].y, ay2[k].y, az2[k].y);
+                    if (NF_PAIRED_FOLD) {
+                        comp_fold_smem2(comp + comp_slot(lane, 2 * k), ax2[k], ay2[k], az2[k]);
+                    } else {
+                        comp_fold_smem(comp + comp_slot(lane, 2 * k), ax2[k].x, ay2[k].x, az2[k].x);
+                        comp_fold_smem(comp + comp_slot(lane, 2 * k + 1), ax2[k].y, ay2[k].y, az2[k].y);
+                    }
                 }
             } else {
 #pragma unroll
-                for (int s = 0; s < SS; ++s) comp_fold_smem(comp + lane + 32 * s, px[s], py[s], pz[s]);
+                for (int s = 0; s < SS; ++s) comp_fold_smem(comp + comp_slot(lane, s), px[s], py[s], pz[s]);
             }
         }
         __syncwarp();
@@ -988,7 +1025,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
             for (int s = 0; s < SS; ++s) {
                 mx[s] *= kForceSigma; my[s] *= kForceSigma; mz[s] *= kForceSigma;
                 if (COMP) {
-                    comp_fold_smem(comp + lane + 32 * s, mx[s], my[s], mz[s]);
+                    comp_fold_smem(comp + comp_slot(lane, s), mx[s], my[s], mz[s]);
                 } else {
                     px[s] += mx[s]; py[s] += my[s]; pz[s] += mz[s];
                     mx[s] = my[s] = mz[s] = 0.f;
@@ -1001,7 +1038,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
 #pragma unroll
     for (int s = 0; s < SS; ++s) {
         if (COMP) {
-            const float *c = comp + lane + 32 * s;
+            const float *c = comp + comp_slot(lane, s);
             acc[s].hx = c[0]; acc[s].hy = c[128]; acc[s].hz = c[256];
             acc[s].lx = c[384]; acc[s].ly = c[512]; acc[s].lz = c[640];
         } else {
