@@ -101,9 +101,6 @@ namespace {
 #ifndef NF_LANE_PAIR_UNROLL
 #define NF_LANE_PAIR_UNROLL 2   // paired lane items: source pairs per unrolled step (1 or 2)
 #endif
-#ifndef NF_SHIFT_TABLE
-#define NF_SHIFT_TABLE 1   // the shift pass reads each entry's cell offset from a per-block table
-#endif
 #ifndef NF_FOLD_HALVES
 #define NF_FOLD_HALVES 1   // one-sink lanes add their two source-pair halves before the compensated fold
 #endif
@@ -482,8 +479,9 @@ __device__ __forceinline__ int find_cell(const int *tpre, int f)
 }
 
 // Gather sources [base, base + B) of the flattened neighbourhood into buf
-// (cp.async); entries past `total` become far-away padding.  The offset code
-// of each gathered entry's cell (plus one; 0 = padding) goes to ts[] for the shift pass.
+// (cp.async); entries past `total` become far-away padding.  The neighbour-table
+// position of each gathered entry's cell (plus one; 0 = padding) goes to ts[]
+// for the shift pass.
 template <int B, bool ADJ>
 __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float4 *wbuf, const int *tstart,
                                             const int *tpre, int base, int total, int lane, unsigned char *ts)
@@ -506,7 +504,7 @@ __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float
                 const int src = tstart[p] + (f - tpre[p]);
                 cp_async16(buf + slot, bx.pos + src);
                 if (ADJ) cp_async16(wbuf + slot, bx.cot + src);
-                ts[slot] = static_cast<unsigned char>(__ldg(&kNbrOrder.code[p]) + 1);
+                ts[slot] = static_cast<unsigned char>(p + 1);
             } else {
                 buf[slot] = make_float4(kFar, kFar, kFar, 0.f);
                 if (ADJ) wbuf[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -525,7 +523,7 @@ __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float
             const int src = tstart[p] + (f - tpre[p]);
             cp_async16(buf + slot, bx.pos + src);
             if (ADJ) cp_async16(wbuf + slot, bx.cot + src);
-            ts[slot] = static_cast<unsigned char>(__ldg(&kNbrOrder.code[p]) + 1);
+            ts[slot] = static_cast<unsigned char>(p + 1);
         } else {
             buf[slot] = make_float4(kFar, kFar, kFar, 0.f);
             if (ADJ) wbuf[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -535,52 +533,24 @@ __device__ __forceinline__ void stage_issue(const BoxDev &bx, float4 *buf, float
     cp_async_commit();
 }
 
-// add the integer cell offset of each of this lane's landed entries; with SOA
-// the round is then rewritten in place as three arrays x[B], y[B], z[B] (the
-// layout the source-paired loops read two sources at a time from)
+// add the integer cell offset of each of this lane's landed entries, read from
+// the per-block table offtab (offtab[p + 1] = offset of neighbour-table position
+// p, offtab[0] = 0 for padding); with SOA the round is then rewritten in place
+// as three arrays x[B], y[B], z[B] (the layout the source-paired loops read two
+// sources at a time from)
 template <int B, bool SOA>
 __device__ __forceinline__ void stage_shift(float4 *buf, int lane, const unsigned char *ts, const float4 *offtab)
 {
-    if (NF_SHIFT_TABLE) {
-        // offtab[t1]: the cell offset of table code t1 - 1 (offtab[0] = 0 for padding entries)
-        float4 v[B / 32];
+    float4 v[B / 32];
 #pragma unroll
-        for (int m = 0; m < B / 32; ++m) {
-            const float4 o = offtab[ts[m * 32 + lane]];
-            v[m] = buf[m * 32 + lane];
-            v[m].x += o.x;
-            v[m].y += o.y;
-            v[m].z += o.z;
-        }
-        if constexpr (SOA) {
-            __syncwarp();   // every lane has read its entries before any array entry is written over them
-            float *xs = reinterpret_cast<float *>(buf);
-#pragma unroll
-            for (int m = 0; m < B / 32; ++m) {
-                const int slot = m * 32 + lane;
-                xs[slot] = v[m].x;
-                xs[B + slot] = v[m].y;
-                xs[2 * B + slot] = v[m].z;
-            }
-        } else {
-#pragma unroll
-            for (int m = 0; m < B / 32; ++m) buf[m * 32 + lane] = v[m];
-        }
-        return;
+    for (int m = 0; m < B / 32; ++m) {
+        const float4 o = offtab[ts[m * 32 + lane]];
+        v[m] = buf[m * 32 + lane];
+        v[m].x += o.x;
+        v[m].y += o.y;
+        v[m].z += o.z;
     }
     if constexpr (SOA) {
-        float4 v[B / 32];
-#pragma unroll
-        for (int m = 0; m < B / 32; ++m) {
-            const int t1 = ts[m * 32 + lane];
-            v[m] = buf[m * 32 + lane];
-            if (t1) {
-                const int t = t1 - 1;
-                v[m].x += static_cast<float>(t / 25 - 2);
-                v[m].y += static_cast<float>((t / 5) % 5 - 2);
-                v[m].z += static_cast<float>(t % 5 - 2);
-            }
-        }
         __syncwarp();   // every lane has read its entries before any array entry is written over them
         float *xs = reinterpret_cast<float *>(buf);
 #pragma unroll
@@ -592,17 +562,7 @@ __device__ __forceinline__ void stage_shift(float4 *buf, int lane, const unsigne
         }
     } else {
 #pragma unroll
-        for (int m = 0; m < B / 32; ++m) {
-            const int t1 = ts[m * 32 + lane];
-            if (t1) {
-                const int t = t1 - 1;
-                float4 v = buf[m * 32 + lane];
-                v.x += static_cast<float>(t / 25 - 2);
-                v.y += static_cast<float>((t / 5) % 5 - 2);
-                v.z += static_cast<float>(t % 5 - 2);
-                buf[m * 32 + lane] = v;
-            }
-        }
+        for (int m = 0; m < B / 32; ++m) buf[m * 32 + lane] = v[m];
     }
 }
 
@@ -1348,7 +1308,7 @@ __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
         bx.acc_out[i] = make_float4(static_cast<float>(gx), static_cast<float>(gy), static_cast<float>(gz), 0.f);
 }
 
-constexpr int kOffTab = 128;   // entries of the per-block cell-offset table (codes 0..124, plus one)
+constexpr int kOffTab = 128;   // entries of the per-block cell-offset table (positions 0..124, plus one)
 
 // per-warp shared memory, in float4 units: staged sources (and cotangents),
 // compensated sums, neighbour table (256 ints), table slots (2 B bytes)
@@ -1381,18 +1341,19 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
     int *tabs = reinterpret_cast<int *>(w0 + (ADJ ? 4 : 2) * B + (COMP ? 192 : 0));
     int *tstart = tabs, *tpre = tabs + 128;
     unsigned char *tslot = reinterpret_cast<unsigned char *>(tabs + 256);
-    // after every warp's area: the cell offset of each neighbour-table code (index code + 1; 0: padding)
+    // after every warp's area: the cell offset of each neighbour-table position (index
+    // position + 1; 0: padding)
     float4 *offtab = smem_f4 + (blockDim.x >> 5) * per_warp_f4<B, COMP, ADJ>();
-    if (NF_SHIFT_TABLE) {
-        for (int t1 = threadIdx.x; t1 < kOffTab; t1 += blockDim.x) {
-            const int t = t1 - 1;
-            offtab[t1] = t1 == 0 || t1 > kNbr ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                              : make_float4(static_cast<float>(t / 25 - 2),
-                                                            static_cast<float>((t / 5) % 5 - 2),
-                                                            static_cast<float>(t % 5 - 2), 0.f);
+    for (int t1 = threadIdx.x; t1 < kOffTab; t1 += blockDim.x) {
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t1 >= 1 && t1 <= kNbr) {
+            const int t = kNbrOrder.code[t1 - 1];
+            o = make_float4(static_cast<float>(t / 25 - 2), static_cast<float>((t / 5) % 5 - 2),
+                            static_cast<float>(t % 5 - 2), 0.f);
         }
-        __syncthreads();
+        offtab[t1] = o;
     }
+    __syncthreads();
     const int n_items = *n_items_p;
     long long life0 = 0;
     unsigned long long wall0 = 0;
@@ -1452,8 +1413,7 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
 template <int B, bool COMP, bool ADJ>
 size_t smem_bytes(int warps)
 {
-    return (static_cast<size_t>(warps) * per_warp_f4<B, COMP, ADJ>() + (NF_SHIFT_TABLE ? kOffTab : 0)) *
-           sizeof(float4);
+    return (static_cast<size_t>(warps) * per_warp_f4<B, COMP, ADJ>() + kOffTab) * sizeof(float4);
 }
 
 // Occupancy of one instantiation at `warps` warps per block on the current

@@ -548,3 +548,62 @@ def test_giant_cell_splits_across_pieces_and_cells():
     assert s["rms_rel"] <= RMS_TOL and s["max_bound_ratio"] <= BOUND_K, s
     assert nf.pair_count() == oracle.pair_count(b)
 
+
+
+# ------------------------------------------------------------------ stored positions' fourth word
+
+def test_stored_cell_z_index_stays_internal():
+    """The library keeps each particle's cell z index in the fourth word of its stored
+    position (lane items read source z offsets from it); every load, binning and drift must
+    write it, and nf_get_particles must hand back the documented pad 0, to host and to
+    device memory alike."""
+    torch = require_cuda()
+    import paper_1810_02916_b300 as nfb
+    cpd, eps = 9, 1e-3
+    rng = np.random.default_rng(91)
+    X = rng.random((30000, 3))
+    nf = make_box(X, cpd, eps)
+    b = oracle_side(X, cpd)
+    ref = oracle.forces(b, eps)
+
+    def check(tag):
+        st = nf.get_particles()
+        assert not st["pos"][:, 3].any(), tag
+        dev = torch.full((nf.n, 4), 7.0, dtype=torch.float32, device="cuda")
+        nf._call("nf_get_particles", None, None, nfb._ptr(dev), None, None)
+        got = dev.cpu().numpy()
+        assert not got[:, 3].any(), tag
+        assert np.array_equal(got[:, :3], st["pos"][:, :3]), tag
+        return st
+
+    st = check("after binning")
+    assert np.array_equal(st["pos"][:, :3], b.xq.astype(np.float32))
+    # a caller-binned load with garbage in the pad word: ignored on input, 0 on output
+    pos = st["pos"].copy()
+    pos[:, 3] = rng.standard_normal(nf.n).astype(np.float32)
+    nf.set_particles(st["cell_offsets"], st["counts"], pos)
+    check("after nf_set_particles")
+    acc = nf.forces()
+    s = oracle.error_stats(acc[:, :3], ref)
+    assert s["rms_rel"] <= RMS_TOL, s
+    # a step that moves every particle up to 0.4 cell widths per axis (many change cells) while
+    # the kick moves it by at most 0.01 cell widths
+    w = 1.0 / cpd
+    dt = float(np.sqrt(0.01 * w / np.abs(nf.forces64()).max()))
+    vel = np.zeros((nf.n, 4), np.float32)
+    vel[:, :3] = (rng.uniform(-0.4, 0.4, (nf.n, 3)) * w / dt).astype(np.float32)
+    nf.set_velocities(vel)
+    nf.kick_drift(dt)
+    st2 = check("after a drift")
+    moved = np.repeat(np.arange(cpd ** 3), np.diff(st2["cell_offsets"]))[np.argsort(st2["perm"])]
+    before = np.repeat(np.arange(cpd ** 3), np.diff(st["cell_offsets"]))   # ids = storage order of the load
+    assert (moved != before).mean() > 0.2
+    # forces after the drift (its re-binning wrote the new cells' z) against the oracle on the
+    # box's own state
+    counts = st2["counts"].astype(np.int64)
+    b2 = oracle.Binned(cpd=cpd, box=1.0, order=st2["perm"].astype(np.int64),
+                       cell=np.repeat(np.arange(cpd ** 3), counts), xq=st2["pos"][:, :3].copy(),
+                       offsets=st2["cell_offsets"].astype(np.int64), counts=counts)
+    acc2 = nf.forces()
+    s2 = oracle.error_stats(acc2[:, :3], oracle.forces(b2, eps))
+    assert s2["rms_rel"] <= RMS_TOL, s2
