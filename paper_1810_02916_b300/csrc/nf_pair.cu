@@ -107,11 +107,17 @@ namespace {
 #ifndef NF_PAIRED_FOLD
 #define NF_PAIRED_FOLD 1   // lanes with 2 or 4 sinks fold two sinks' partials per paired FP32 instruction
 #endif
+#ifndef NF_SINGLE_STAGE
+#define NF_SINGLE_STAGE 0   // forces stage one round at a time (no double buffer): less shared memory per warp
+#endif
 #ifndef NF_UNROLL_S2
 #define NF_UNROLL_S2 NF_SRC_UNROLL   // staged sources per unrolled step on lanes holding two sinks
 #endif
 
 constexpr unsigned kFull = 0xffffffffu;
+// staging buffers per warp: two (the next round loads while this one is computed), or one
+// for forces with NF_SINGLE_STAGE (other warps cover the load latency)
+__host__ __device__ constexpr int stage_bufs(bool adj) { return (NF_SINGLE_STAGE && !adj) ? 1 : 2; }
 constexpr float kFar = 1.0e18f;   // padding source: y^3 underflows to 0, contributes exactly zero
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
@@ -700,11 +706,17 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
     }
     const int rounds = src_hi > src_lo ? (src_hi - src_lo + B - 1) / B : 0;
 
-    if (rounds > 0) stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, src_lo, src_hi, lane, tslot);
+    constexpr int NBUF = stage_bufs(ADJ);
+    if (NBUF == 2 && rounds > 0) stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, src_lo, src_hi, lane, tslot);
     for (int r = 0; r < rounds; ++r) {
-        float4 *buf = stage + (r & 1) * B;
-        float4 *wbuf = wstage + (r & 1) * B;
-        if (r + 1 < rounds) {
+        const int bsel = NBUF == 2 ? (r & 1) : 0;
+        float4 *buf = stage + bsel * B;
+        float4 *wbuf = wstage + bsel * B;
+        if (NBUF == 1) {
+            // the previous round's readers are done (the __syncwarp closing every round)
+            stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, src_lo + r * B, src_hi, lane, tslot);
+            cp_async_wait_0();
+        } else if (r + 1 < rounds) {
             stage_issue<B, ADJ>(bx, stage + ((r + 1) & 1) * B, wstage + ((r + 1) & 1) * B, tstart, tpre,
                                 src_lo + (r + 1) * B, src_hi, lane, tslot + ((r + 1) & 1) * B);
             cp_async_wait_1();
@@ -714,7 +726,7 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
         // the shift pass reads entries other lanes copied (contiguous staging): their copies are
         // complete once each lane has passed its wait
         if (NF_STAGE_CONTIG) __syncwarp();
-        stage_shift<B, PAIRSRC>(buf, lane, tslot + (r & 1) * B, offtab);
+        stage_shift<B, PAIRSRC>(buf, lane, tslot + bsel * B, offtab);
         __syncwarp();
         const int nr = min(B, src_hi - src_lo - r * B);
         // this round's entries [0, nn) come from the 27 near cells and take the
@@ -966,19 +978,27 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
             if (ts > -2) continue;
             const float4 *src = reinterpret_cast<const float4 *>(bx.mpole) +
                                 static_cast<int64_t>(-2 - ts) * (kCutSub * kCutWords / 4);
-            __syncwarp();
-            for (int k = lane; k < kCutSub * kCutWords / 4; k += 32) stage[k] = __ldg(src + k);
-            __syncwarp();
             const int t = __ldg(&kNbrOrder.code[pp]);
             const float ox = static_cast<float>(t / 25 - 2), oy = static_cast<float>((t / 5) % 5 - 2),
                         oz = static_cast<float>(t % 5 - 2);
-            for (int q = q0; q < kCutSub; q += dq) {
-                const float *o = moments + q * kCutWords;
-                const float M = o[0];
-                if (M == 0.f) continue;
-                const float cx = o[1] + ox, cy = o[2] + oy, cz = o[3] + oz;
+            // the sub-cells' words in chunks that fit the staged-source buffers (sub-cells in order)
+            constexpr int kChunks = 2 / stage_bufs(ADJ), kSubPer = kCutSub / kChunks;
+            static_assert(kSubPer * kCutWords / 4 <= stage_bufs(ADJ) * B, "moment chunk exceeds the staging area");
+            int q = q0;
+            for (int ch = 0; ch < kChunks; ++ch) {
+                __syncwarp();
+                for (int k = lane; k < kSubPer * kCutWords / 4; k += 32)
+                    stage[k] = __ldg(src + ch * (kSubPer * kCutWords / 4) + k);
+                __syncwarp();
+                for (; q < (ch + 1) * kSubPer; q += dq) {
+                    const float *o = moments + (q - ch * kSubPer) * kCutWords;
+                    const float M = o[0];
+                    if (M == 0.f) continue;
+                    const float cx = o[1] + ox, cy = o[2] + oy, cz = o[3] + oz;
 #pragma unroll
-                for (int s = 0; s < SS; ++s) quad_force(cx - sxp[s], cy - syp[s], cz - szp[s], M, o + 4, mx[s], my[s], mz[s]);
+                    for (int s = 0; s < SS; ++s)
+                        quad_force(cx - sxp[s], cy - syp[s], cz - szp[s], M, o + 4, mx[s], my[s], mz[s]);
+                }
             }
             // one FP32 partial per dense cell, in the accumulators' scale, folded like a round of sources
 #pragma unroll
@@ -1311,11 +1331,11 @@ __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
 constexpr int kOffTab = 128;   // entries of the per-block cell-offset table (positions 0..124, plus one)
 
 // per-warp shared memory, in float4 units: staged sources (and cotangents),
-// compensated sums, neighbour table (256 ints), table slots (2 B bytes)
+// compensated sums, neighbour table (256 ints), table slots (B bytes per staging buffer)
 template <int B, bool COMP, bool ADJ>
 __host__ __device__ constexpr int per_warp_f4()
 {
-    return (ADJ ? 4 : 2) * B + (COMP ? 192 : 0) + 64 + B / 8;
+    return (ADJ ? 2 : 1) * stage_bufs(ADJ) * B + (COMP ? 192 : 0) + 64 + stage_bufs(ADJ) * B / 16;
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -1326,7 +1346,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 template <int B, bool COMP, bool ADJ, int SOFT>
-__global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *__restrict__ boxes,
+__global__ void __launch_bounds__(256, ADJ ? 3 : NF_MIN_BLOCKS) pair_kernel(const BoxDev *__restrict__ boxes,
                                                                   const Item *__restrict__ items,
                                                                   const int *__restrict__ n_items_p,
                                                                   int *__restrict__ queue,
@@ -1336,9 +1356,10 @@ __global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *w0 = smem_f4 + warp * per_warp_f4<B, COMP, ADJ>();
     float4 *stage = w0;
-    float4 *wstage = stage + 2 * B;
-    float *comp = reinterpret_cast<float *>(w0 + (ADJ ? 4 : 2) * B);
-    int *tabs = reinterpret_cast<int *>(w0 + (ADJ ? 4 : 2) * B + (COMP ? 192 : 0));
+    constexpr int SB = (ADJ ? 2 : 1) * stage_bufs(ADJ) * B;   // staged sources (and cotangents)
+    float4 *wstage = stage + stage_bufs(ADJ) * B;
+    float *comp = reinterpret_cast<float *>(w0 + SB);
+    int *tabs = reinterpret_cast<int *>(w0 + SB + (COMP ? 192 : 0));
     int *tstart = tabs, *tpre = tabs + 128;
     unsigned char *tslot = reinterpret_cast<unsigned char *>(tabs + 256);
     // after every warp's area: the cell offset of each neighbour-table position (index
