@@ -95,9 +95,6 @@ namespace {
 #ifndef NF_LANE_PAIRED
 #define NF_LANE_PAIRED 1   // lane items of library-loaded boxes: z offsets from w, two sources per paired instruction
 #endif
-#ifndef NF_LANE_PREFETCH
-#define NF_LANE_PREFETCH 0   // paired lane items load the next column's cell bounds during the current column
-#endif
 #ifndef NF_LANE_PAIR_UNROLL
 #define NF_LANE_PAIR_UNROLL 2   // paired lane items: source pairs per unrolled step (1 or 2)
 #endif
@@ -107,17 +104,11 @@ namespace {
 #ifndef NF_PAIRED_FOLD
 #define NF_PAIRED_FOLD 1   // lanes with 2 or 4 sinks fold two sinks' partials per paired FP32 instruction
 #endif
-#ifndef NF_SINGLE_STAGE
-#define NF_SINGLE_STAGE 0   // forces stage one round at a time (no double buffer): less shared memory per warp
-#endif
 #ifndef NF_UNROLL_S2
 #define NF_UNROLL_S2 NF_SRC_UNROLL   // staged sources per unrolled step on lanes holding two sinks
 #endif
 
 constexpr unsigned kFull = 0xffffffffu;
-// staging buffers per warp: two (the next round loads while this one is computed), or one
-// for forces with NF_SINGLE_STAGE (other warps cover the load latency)
-__host__ __device__ constexpr int stage_bufs(bool adj) { return (NF_SINGLE_STAGE && !adj) ? 1 : 2; }
 constexpr float kFar = 1.0e18f;   // padding source: y^3 underflows to 0, contributes exactly zero
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
@@ -706,17 +697,12 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
     }
     const int rounds = src_hi > src_lo ? (src_hi - src_lo + B - 1) / B : 0;
 
-    constexpr int NBUF = stage_bufs(ADJ);
-    if (NBUF == 2 && rounds > 0) stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, src_lo, src_hi, lane, tslot);
+    if (rounds > 0) stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, src_lo, src_hi, lane, tslot);
     for (int r = 0; r < rounds; ++r) {
-        const int bsel = NBUF == 2 ? (r & 1) : 0;
+        const int bsel = r & 1;
         float4 *buf = stage + bsel * B;
         float4 *wbuf = wstage + bsel * B;
-        if (NBUF == 1) {
-            // the previous round's readers are done (the __syncwarp closing every round)
-            stage_issue<B, ADJ>(bx, stage, wstage, tstart, tpre, src_lo + r * B, src_hi, lane, tslot);
-            cp_async_wait_0();
-        } else if (r + 1 < rounds) {
+        if (r + 1 < rounds) {
             stage_issue<B, ADJ>(bx, stage + ((r + 1) & 1) * B, wstage + ((r + 1) & 1) * B, tstart, tpre,
                                 src_lo + (r + 1) * B, src_hi, lane, tslot + ((r + 1) & 1) * B);
             cp_async_wait_1();
@@ -981,24 +967,18 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
             const int t = __ldg(&kNbrOrder.code[pp]);
             const float ox = static_cast<float>(t / 25 - 2), oy = static_cast<float>((t / 5) % 5 - 2),
                         oz = static_cast<float>(t % 5 - 2);
-            // the sub-cells' words in chunks that fit the staged-source buffers (sub-cells in order)
-            constexpr int kChunks = 2 / stage_bufs(ADJ), kSubPer = kCutSub / kChunks;
-            static_assert(kSubPer * kCutWords / 4 <= stage_bufs(ADJ) * B, "moment chunk exceeds the staging area");
-            int q = q0;
-            for (int ch = 0; ch < kChunks; ++ch) {
-                __syncwarp();
-                for (int k = lane; k < kSubPer * kCutWords / 4; k += 32)
-                    stage[k] = __ldg(src + ch * (kSubPer * kCutWords / 4) + k);
-                __syncwarp();
-                for (; q < (ch + 1) * kSubPer; q += dq) {
-                    const float *o = moments + (q - ch * kSubPer) * kCutWords;
-                    const float M = o[0];
-                    if (M == 0.f) continue;
-                    const float cx = o[1] + ox, cy = o[2] + oy, cz = o[3] + oz;
+            // the dense cell's sub-cell words fit the two staging buffers
+            static_assert(kCutSub * kCutWords / 4 <= 2 * B, "moments exceed the staging area");
+            __syncwarp();
+            for (int k = lane; k < kCutSub * kCutWords / 4; k += 32) stage[k] = __ldg(src + k);
+            __syncwarp();
+            for (int q = q0; q < kCutSub; q += dq) {
+                const float *o = moments + q * kCutWords;
+                const float M = o[0];
+                if (M == 0.f) continue;
+                const float cx = o[1] + ox, cy = o[2] + oy, cz = o[3] + oz;
 #pragma unroll
-                    for (int s = 0; s < SS; ++s)
-                        quad_force(cx - sxp[s], cy - syp[s], cz - szp[s], M, o + 4, mx[s], my[s], mz[s]);
-                }
+                for (int s = 0; s < SS; ++s) quad_force(cx - sxp[s], cy - syp[s], cz - szp[s], M, o + 4, mx[s], my[s], mz[s]);
             }
             // one FP32 partial per dense cell, in the accumulators' scale, folded like a round of sources
 #pragma unroll
@@ -1103,30 +1083,12 @@ __device__ void run_lanes_paired(const BoxDev &bx, const Item &item, int lane)
     const float2 npz = make_float2(-p.z, -p.z);
     Comp3 acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const bool wrap_lo = cz < 2, wrap_hi = cz + 3 > C;   // never both: C >= 5
-    // the first run of every column spans cells [zr0, zr1) of the column's row
-    const int zr0 = wrap_lo ? cz - 2 + C : cz - 2, zr1 = wrap_lo ? C : min(cz + 3, C);
-    auto row_of = [&](int col) {
-        int nx = cx + col / 5 - 2, ny = cy + col % 5 - 2;
-        nx += nx < 0 ? C : 0; nx -= nx >= C ? C : 0;
-        ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
-        return cs + (nx * C + ny) * C;
-    };
-    // NF_LANE_PREFETCH: the next column's first-run bounds are loaded while this column runs
-    int jn0 = 0, jn1 = 0;
-    if (NF_LANE_PREFETCH) {
-        const int *row0 = row_of(0);
-        jn0 = __ldg(row0 + zr0);
-        jn1 = __ldg(row0 + zr1);
-    }
     for (int col = 0; col < 25; ++col) {
         const int dxi = col / 5 - 2, dyi = col % 5 - 2;
-        const int *row = row_of(col);
-        int jc0 = jn0, jc1 = jn1;
-        if (NF_LANE_PREFETCH && col + 1 < 25) {
-            const int *rown = row_of(col + 1);
-            jn0 = __ldg(rown + zr0);
-            jn1 = __ldg(rown + zr1);
-        }
+        int nx = cx + dxi, ny = cy + dyi;
+        nx += nx < 0 ? C : 0; nx -= nx >= C ? C : 0;
+        ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
+        const int *row = cs + (nx * C + ny) * C;
         const float ox = static_cast<float>(dxi) - p.x, oy = static_cast<float>(dyi) - p.y;   // exact
         const float2 ox2 = make_float2(ox, ox), oy2 = make_float2(oy, oy);
         // warp-uniform (every lane walks the columns in the same order)
@@ -1145,14 +1107,7 @@ __device__ void run_lanes_paired(const BoxDev &bx, const Item &item, int lane)
                 z1 = wrap_lo ? cz + 3 : cz + 3 - C;
                 zoff = wrap_lo ? -cz : C - cz;
             }
-            int j0, j1;
-            if (NF_LANE_PREFETCH && part == 0) {
-                j0 = jc0;
-                j1 = jc1;
-            } else {
-                j0 = __ldg(row + z0);
-                j1 = __ldg(row + z1);
-            }
+            const int j0 = __ldg(row + z0), j1 = __ldg(row + z1);
             const float2 zo2 = make_float2(static_cast<float>(zoff), static_cast<float>(zoff));
             // one source pair: (w + zoff) is the integer z offset; minus x_i, plus x_j: each step exact
             auto pair = [&](const float4 &q0, const float4 &q1) {
@@ -1331,11 +1286,11 @@ __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
 constexpr int kOffTab = 128;   // entries of the per-block cell-offset table (positions 0..124, plus one)
 
 // per-warp shared memory, in float4 units: staged sources (and cotangents),
-// compensated sums, neighbour table (256 ints), table slots (B bytes per staging buffer)
+// compensated sums, neighbour table (256 ints), table slots (B bytes for each of the two buffers)
 template <int B, bool COMP, bool ADJ>
 __host__ __device__ constexpr int per_warp_f4()
 {
-    return (ADJ ? 2 : 1) * stage_bufs(ADJ) * B + (COMP ? 192 : 0) + 64 + stage_bufs(ADJ) * B / 16;
+    return (ADJ ? 4 : 2) * B + (COMP ? 192 : 0) + 64 + B / 8;
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -1346,7 +1301,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 template <int B, bool COMP, bool ADJ, int SOFT>
-__global__ void __launch_bounds__(256, ADJ ? 3 : NF_MIN_BLOCKS) pair_kernel(const BoxDev *__restrict__ boxes,
+__global__ void __launch_bounds__(256, NF_MIN_BLOCKS) pair_kernel(const BoxDev *__restrict__ boxes,
                                                                   const Item *__restrict__ items,
                                                                   const int *__restrict__ n_items_p,
                                                                   int *__restrict__ queue,
@@ -1356,8 +1311,8 @@ __global__ void __launch_bounds__(256, ADJ ? 3 : NF_MIN_BLOCKS) pair_kernel(cons
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *w0 = smem_f4 + warp * per_warp_f4<B, COMP, ADJ>();
     float4 *stage = w0;
-    constexpr int SB = (ADJ ? 2 : 1) * stage_bufs(ADJ) * B;   // staged sources (and cotangents)
-    float4 *wstage = stage + stage_bufs(ADJ) * B;
+    constexpr int SB = (ADJ ? 4 : 2) * B;   // two buffers of staged sources (and cotangents)
+    float4 *wstage = stage + 2 * B;
     float *comp = reinterpret_cast<float *>(w0 + SB);
     int *tabs = reinterpret_cast<int *>(w0 + SB + (COMP ? 192 : 0));
     int *tstart = tabs, *tpre = tabs + 128;
