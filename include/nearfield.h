@@ -175,8 +175,9 @@ int nf_set_velocities(nf_t *nf, const float *vel);
 /*
  * nf_get_particles -- read the state back (checkpoint).  Any output may be
  * NULL.  cell_offsets: cpd^3 + 1 int64; counts: cpd^3 int32; pos, vel:
- * n x 4 floats as in nf_set_particles / nf_set_velocities; perm: n int64,
- * perm[k] = id of the particle stored at k.  Synchronises.
+ * n x 4 floats as in nf_set_particles / nf_set_velocities (the fourth word
+ * of pos is 0); perm: n int64, perm[k] = id of the particle stored at k.
+ * Host or device memory.  Synchronises.
  */
 int nf_get_particles(nf_t *nf, int64_t *cell_offsets, int32_t *counts, float *pos,
                      float *vel, int64_t *perm);
