@@ -1056,10 +1056,11 @@ __device__ int run_item(const BoxDev &bx, const Item &item, float4 *stage, float
 // Forces of a lane item when every stored position carries its cell's z index
 // in w (BoxDev::zcell, boxes the library loaded).  Each lane walks its 25
 // (dx, dy) columns as run_lanes does, but a source's z offset is w + zoff (an
-// exact small integer; zoff is constant over a column's run, which does not
-// wrap), so a column needs only the two cell boundaries of its run, and each
-// lane evaluates two consecutive sources per paired FP32 instruction (an odd
-// last source is paired with far-away padding, an exact zero).  Separations
+// exact small integer; zoff is constant over each contiguous run of a column,
+// two runs where the column wraps the box in z), so a run needs only its two
+// cell boundaries, and each lane evaluates two consecutive sources per paired
+// FP32 instruction, two such pairs per step (an odd last source is paired with
+// far-away padding, an exact zero; a second pair with no source is skipped).  Separations
 // stay exact: (w + zoff) - x_i and x_j + that are sums on the 2^-22 grid below
 // 4 in magnitude.  Columns at |dx| = 2 or |dy| = 2 take the Newtonian law;
 // in the others a source pair takes the branch-free law only when one of its
@@ -1175,7 +1176,8 @@ __device__ void run_lanes_paired(const BoxDev &bx, const Item &item, int lane)
 // source's dz follows from the cell boundaries inside the run.  Separations are
 // exact as on the staged path: (x_j + D) - x_i on the 2^-22 grid.  Lanes work
 // independently (no warp-synchronous step); columns at |dx| = 2 or |dy| = 2
-// take the Newtonian law, the others the branch-free law.
+// take the Newtonian law, the others the branch-free law.  Used by the adjoint
+// and by boxes whose positions lack the z index (nf_forces_noalloc).
 template <bool COMP, bool ADJ, int SOFT>
 __device__ void run_lanes(const BoxDev &bx, const Item &item, int lane)
 {
