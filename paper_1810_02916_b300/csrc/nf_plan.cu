@@ -169,34 +169,45 @@ __global__ void advance_base(int *__restrict__ base_p, const int *__restrict__ o
 
 __global__ void zero_int(int *p) { *p = 0; }
 
-// (2 radius + 1)-point periodic window sum along one axis of a cpd^3 array
-__global__ void window_sum(const int *__restrict__ in, int *__restrict__ out, int cpd, int axis, int radius)
+// Sum over the 2 radius + 1 cells along z (periodic) of the cell occupancy, read
+// straight from cell_start; with n_min > 0 only the cells below n_min (dense = 0)
+// or only those at or above it (dense = 1) count.  Indices fit 32 bits (cpd^3 < 2^31).
+__global__ void window_z_occ(const int *__restrict__ cell_start, int cpd, int64_t n_min, int dense, int radius,
+                             int *__restrict__ out)
 {
-    const int64_t ncell = static_cast<int64_t>(cpd) * cpd * cpd;
-    const int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int z = static_cast<int>(c % cpd), y = static_cast<int>((c / cpd) % cpd);
-    const int x = static_cast<int>(c / (static_cast<int64_t>(cpd) * cpd));
+    const unsigned C = static_cast<unsigned>(cpd);
+    const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C * C * C) return;
+    const unsigned row = c / C, z = c - row * C;
+    const int *rs = cell_start + row * C;
     int s = 0;
     for (int d = -radius; d <= radius; ++d) {
-        int xx = x, yy = y, zz = z;
-        if (axis == 0) xx = (x + d + cpd) % cpd;
-        else if (axis == 1) yy = (y + d + cpd) % cpd;
-        else zz = (z + d + cpd) % cpd;
-        s += in[(static_cast<int64_t>(xx) * cpd + yy) * cpd + zz];
+        int zz = static_cast<int>(z) + d;
+        zz += zz < 0 ? cpd : 0;
+        zz -= zz >= cpd ? cpd : 0;
+        const int n = rs[zz + 1] - rs[zz];
+        s += (n_min <= 0 || (n >= n_min) == (dense != 0)) ? n : 0;
     }
     out[c] = s;
 }
 
-// occupancy of every cell; with n_min > 0 only the cells below n_min (dense = 0)
-// or only those at or above it (dense = 1), zero elsewhere
-__global__ void occupancy(const int *__restrict__ cell_start, int ncell, int64_t n_min, int dense,
-                          int *__restrict__ occ)
+// Sum over the 2 radius + 1 cells along y (axis 1) or x (axis 0), periodic.
+__global__ void window_yx(const int *__restrict__ in, int *__restrict__ out, int cpd, int axis, int radius)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int n = cell_start[c + 1] - cell_start[c];
-    occ[c] = (n_min <= 0 || (n >= n_min) == (dense != 0)) ? n : 0;
+    const unsigned C = static_cast<unsigned>(cpd);
+    const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C * C * C) return;
+    const unsigned stride = axis == 1 ? C : C * C;
+    const unsigned a = axis == 1 ? (c / C) % C : c / (C * C);
+    const unsigned base = c - a * stride;
+    int s = 0;
+    for (int d = -radius; d <= radius; ++d) {
+        int aa = static_cast<int>(a) + d;
+        aa += aa < 0 ? cpd : 0;
+        aa -= aa >= cpd ? cpd : 0;
+        s += in[base + static_cast<unsigned>(aa) * stride];
+    }
+    out[c] = s;
 }
 
 __global__ void add_into(int *__restrict__ a, const int *__restrict__ b, int ncell)
@@ -227,13 +238,21 @@ __global__ void dense_slots(const int *__restrict__ cell_start, int ncell, int64
 __global__ void dot_counts(const int *__restrict__ cell_start, const int *__restrict__ nbr, int ncell,
                            unsigned long long *__restrict__ out)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    // grid-stride sum per thread, then one atomic per block
+    __shared__ unsigned long long part[32];
     unsigned long long v = 0;
-    if (c < ncell)
-        v = static_cast<unsigned long long>(cell_start[c + 1] - cell_start[c]) * static_cast<unsigned long long>(nbr[c]);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x)
+        v += static_cast<unsigned long long>(cell_start[c + 1] - cell_start[c]) * static_cast<unsigned long long>(nbr[c]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0 && v) atomicAdd(out, v);
+    }
 }
 
 // ---- source splitting of long items (deterministic: fixed pieces, fixed reduction order)
@@ -499,29 +518,27 @@ cudaError_t neighbour_pairs(const int *cell_start, int cpd, int64_t n_min, unsig
                             int *tmp2, int *nbr, int *nbr_all, cudaStream_t st)
 {
     const int ncell = cpd * cpd * cpd;
+    const int nb = nblocks(ncell, 256);
     if (n_min > 0) {
         // cut-off mode: every particle of the 125-cell window, dense cells included (the
         // lane-item choice must see a dense far cell, which run_lanes would sum pair by pair)
-        occupancy<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, 0, 0, tmp);
-        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr_all, cpd, 2, kR);
-        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(nbr_all, tmp, cpd, 1, kR);
-        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr_all, cpd, 0, kR);
+        window_z_occ<<<nb, 256, 0, st>>>(cell_start, cpd, 0, 0, kR, nbr_all);
+        window_yx<<<nb, 256, 0, st>>>(nbr_all, tmp, cpd, 1, kR);
+        window_yx<<<nb, 256, 0, st>>>(tmp, nbr_all, cpd, 0, kR);
     }
     // cells summed over the whole 125-cell window (all of them, or those below n_min) ...
-    occupancy<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, n_min, 0, tmp);
-    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr, cpd, 2, kR);
-    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(nbr, tmp, cpd, 1, kR);
-    window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, nbr, cpd, 0, kR);
+    window_z_occ<<<nb, 256, 0, st>>>(cell_start, cpd, n_min, 0, kR, nbr);
+    window_yx<<<nb, 256, 0, st>>>(nbr, tmp, cpd, 1, kR);
+    window_yx<<<nb, 256, 0, st>>>(tmp, nbr, cpd, 0, kR);
     if (n_min > 0) {
         // ... and, in cut-off mode, the dense cells over the 27 near cells only
-        occupancy<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, ncell, n_min, 1, tmp);
-        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, tmp2, cpd, 2, 1);
-        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp2, tmp, cpd, 1, 1);
-        window_sum<<<nblocks(ncell, 256), 256, 0, st>>>(tmp, tmp2, cpd, 0, 1);
-        add_into<<<nblocks(ncell, 256), 256, 0, st>>>(nbr, tmp2, ncell);
+        window_z_occ<<<nb, 256, 0, st>>>(cell_start, cpd, n_min, 1, 1, tmp2);
+        window_yx<<<nb, 256, 0, st>>>(tmp2, tmp, cpd, 1, 1);
+        window_yx<<<nb, 256, 0, st>>>(tmp, tmp2, cpd, 0, 1);
+        add_into<<<nb, 256, 0, st>>>(nbr, tmp2, ncell);
     }
     cudaMemsetAsync(pairs, 0, sizeof(unsigned long long), st);
-    dot_counts<<<nblocks(ncell, 256), 256, 0, st>>>(cell_start, nbr, ncell, pairs);
+    dot_counts<<<std::max(1, std::min(nb, 148 * 8)), 256, 0, st>>>(cell_start, nbr, ncell, pairs);
     return cudaGetLastError();
 }
 
